@@ -1,0 +1,294 @@
+"""Benchmark of the HOTRG coarse-graining step (one JSON line on rank 0).
+
+A step is one steady-state half-step of the 2D Ising HOTRG at beta_c with
+Dcut = 64 (environment, isometry, U.T.T.U contraction, normalisation) on a
+resident D = 64 tensor.  Usage:
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision split|fp64]
+  python bench.py --impl reference ...   # the CPU oracle on the host cores
+
+Under torchrun (N > 1) every rank runs an independent solve (replicas; the
+path has no exchange step between solves), timed with a barrier and the max
+over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+DCUT = 64
+BETA_C = 0.5 * math.log(1.0 + math.sqrt(2.0))
+STEADY_AT = 6           # half-steps after which Dx = Dy = 64 (2 -> 4 -> 16 -> 64)
+METRIC = "HOTRG s/step at Dcut=64 (2D Ising, beta_c, half-step)"
+WORKLOAD = "2D Ising, h=0, beta=beta_c=0.4406868, D0=2, Dcut=64, steady-state half-step (Dx=Dy=64)"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=None)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--precision", default=None, choices=["split", "fp64"])
+    ap.add_argument("--slices", type=int, default=4)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--solve", action="store_true", help="also time one full 40-half-step solve")
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------ clocks ---
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        busy = [s for s in sm if s > 0.5 * max(sm)] or sm
+        return {"sm_mhz": statistics.median(busy), "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ----------------------------------------------------------- CPU baseline ---
+def oracle_half_step_sample():
+    """Time the oracle on a bounded sample of one D=64 half-step and scale it
+    to the whole half-step.  Returns (seconds per half-step, description)."""
+    from oracle import hotrg, jacobi
+    from paper_2306_00358_gb300 import workloads
+
+    d = DCUT
+    t = workloads.random_tensor((d, d, d, d), seed=11) * 1e-2
+    u = workloads.random_isometry(d, d, seed=12)
+    # contraction: one j-slice of 64 (the slices are identical in cost)
+    t0 = time.perf_counter()
+    hotrg.contract_x_slice(t, u, 0, 1)
+    t_con = (time.perf_counter() - t0) * d
+    t0 = time.perf_counter()
+    hotrg.environment_x(t)
+    t_env = time.perf_counter() - t0
+    # eigensolve: cyclic Jacobi on a 256 x 256 block of a graded PSD matrix, scaled by n^3
+    nb = 256
+    m = workloads.graded_psd(nb, 16, seed=13)
+    t0 = time.perf_counter()
+    jacobi.eigh(m)
+    t_eig = (time.perf_counter() - t0) * (d * d / nb) ** 3
+    total = t_con + t_env + t_eig
+    desc = (f"oracle at D=64: contraction 1 of 64 j-slices x64 ({t_con:.1f}s), environment in full "
+            f"({t_env:.1f}s), Jacobi on a 256x256 graded block x(4096/256)^3 ({t_eig:.0f}s)")
+    return total, desc
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    steps = args.steps or 3
+    for _ in range(args.warmup):
+        oracle_half_step_sample()
+    t0 = time.perf_counter()
+    vals = []
+    desc = ""
+    for _ in range(steps):
+        v, desc = oracle_half_step_sample()
+        vals.append(v)
+    wall = time.perf_counter() - t0
+    val = statistics.mean(vals)
+    cores = os.cpu_count()
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "s/half-step", "n_gpus": args.gpus,
+            "steps": steps, "warmup": args.warmup, "ms_per_step": val * 1e3, "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD + " (oracle sample, scaled)", "dcut": DCUT},
+            "cpu_baseline": {"value": val, "unit": "s/half-step", "cores": cores, "kind": "oracle", "sample": desc},
+            "e2e": {"value": val, "unit": "s/half-step", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "wall_s": wall}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------- GPU arm -----
+def load_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+def run_native(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_2306_00358_gb300 import Solver
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    precision = args.precision or "fp64"
+    steps = args.steps or (2 if precision == "fp64" else 10)
+    warmup = max(3, args.warmup)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    stream = torch.cuda.current_stream()
+    s = Solver(local, stream=stream, precision=precision, split_slices=args.slices)
+    # replicas: every rank solves its own coupling (beta_c shifted per rank)
+    beta = BETA_C * (1.0 + 1e-4 * rank)
+    s.init_tensor("ising", beta, 0.0)
+    s.coarse_grain(DCUT, STEADY_AT)
+    s.coarse_grain(DCUT, warmup)
+    barrier()
+    s.profile(True)
+    launches0 = s.launch_count()
+    clocks = ClockSampler(local)
+    clocks.start()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    barrier()
+    ev0.record(stream)
+    s.coarse_grain(DCUT, steps)
+    ev1.record(stream)
+    barrier()
+    clk = clocks.stop()
+    ms = ev0.elapsed_time(ev1)
+    launches = s.launch_count() - launches0
+    ph = s.phase_stats()
+    s.profile(False)
+    t_max = torch.tensor([ms], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
+    ms_max = float(t_max.item())
+    sec_per_step = ms_max / 1e3 / (steps * world)
+
+    # roofline of the dominant kernel: the D^7 product
+    peaks = load_peaks()
+    x2 = ph["x2"]
+    if precision == "fp64":
+        per_launch = x2["flops"] / max(1, x2["calls"])
+        t_launch = x2["ms"] / max(1, x2["calls"]) / 1e3
+        achieved = per_launch / t_launch / 1e12
+        # FP64 FMA units: 2 FMA/clk/SM x 152 SMs x 2 flop x max SM clock (nominal 1.25 TF/s)
+        sm_mhz = peaks.get("sm_max_mhz", 2070.0)
+        peak = 152 * 2 * 2 * sm_mhz * 1e6 / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": None, "kernel": "k_gemm_f64 (X2 = X1.t, D^7)",
+                "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x max SM clock"}
+    else:
+        mma = ph["mma"]
+        per_launch = mma["mma_flops"] / max(1, mma["calls"])
+        t_launch = mma["ms"] / max(1, mma["calls"]) / 1e3
+        achieved = per_launch / t_launch / 1e12 if t_launch > 0 else 0.0
+        peak = peaks.get("bf16_tflops_sustained", 1722.5)
+        roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": None, "kernel": "k_split_mma (BF16 slice products)",
+                "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained (of measured)"}
+
+    # end to end through the C ABI with host buffers
+    e2e = None
+    if not args.no_e2e:
+        t_host = s.tensor()
+        h2d = t_host.nbytes
+        s2 = s
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ne = max(1, min(steps, 3))
+        for _ in range(ne):
+            s2.init_tensor_raw(t_host, beta)       # host -> device copy of the step's input
+            s2.coarse_grain(DCUT, 1)
+            f, _ = s2.free_energy()                # device -> host read of the result
+        torch.cuda.synchronize()
+        e2e_s = (time.perf_counter() - t0) / ne
+        e2e = {"value": e2e_s, "unit": "s/half-step", "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": 16 + 8}
+
+    solve = None
+    if args.solve:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        s.init_tensor("ising", beta, 0.0)
+        s.coarse_grain(DCUT, 40)
+        f, _ = s.free_energy()
+        solve = {"seconds": time.perf_counter() - t0, "solves_per_s": 1.0 / (time.perf_counter() - t0), "f": f}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, desc = oracle_half_step_sample()
+        cpu = {"value": v, "unit": "s/half-step", "cores": os.cpu_count(), "kind": "oracle", "sample": desc}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": sec_per_step, "unit": "s/half-step", "n_gpus": world, "steps": steps,
+                "warmup": warmup, "ms_per_step": ms_max / steps, "higher_is_better": False, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f64" if precision == "fp64" else "bf16-slices(x%d)->f64" % args.slices,
+                "data": "synthetic",
+                "config": {"workload": WORKLOAD, "precision": precision, "dcut": DCUT,
+                           "l2": "inputs larger than L2 (T 134 MB, M 134 MB, workspace >= 1 GB per step)",
+                           "parallelism": "replicas" if world > 1 else "single"},
+                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
+                "phases_ms": {k: round(v["ms"], 3) for k, v in ph.items()}, "solve": solve}
+        print(json.dumps(line), flush=True)
+    s.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_native(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,218 @@
+/*
+ * trg.h -- C ABI of the GB300-native HOTRG coarse-graining library (libtrg).
+ *
+ * The library computes the free energy of 2D classical spin models with the
+ * higher-order tensor renormalisation group step of arXiv:2306.00358
+ * ("GPU-Acceleration of Tensor Renormalization with PyTorch using CUDA"),
+ * Sec. 2: the coarse-graining listing (environment einsum, SVD isometry,
+ * U.T.T.U contraction, normalisation) and Fig. 1 (two directional blockings
+ * per iteration, periodic trace after N iterations).  Every step runs in the
+ * library's own CUDA kernels for sm_103a; there is no CPU fallback.
+ *
+ * Conventions
+ *  - Every function returns a trg_status (0 = TRG_OK).  On failure the
+ *    context keeps its previous state where possible and trg_last_error()
+ *    gives a one-line reason.
+ *  - Site tensors are FP64, row-major, legs (left, up, right, down) with
+ *    shape (Dx, Dy, Dx, Dy): element T[l][u][r][d] sits at
+ *    ((l*Dy + u)*Dx + r)*Dy + d.
+ *  - "host" pointers are ordinary CPU memory; "device" pointers are CUDA
+ *    global memory on the context's device.  The library never takes
+ *    ownership of caller buffers; it copies what it keeps.
+ *  - All device work of a context is ordered on one CUDA stream (the
+ *    default stream unless trg_set_stream is called).  Calls on one context
+ *    are not thread-safe; different contexts are independent.
+ *  - Device memory the context needs is allocated through the allocator
+ *    hook (cudaMalloc by default) and freed by trg_destroy.
+ */
+#ifndef TRG_H
+#define TRG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ----------------------------------------------------------- status ----- */
+typedef enum trg_status {
+    TRG_OK = 0,
+    TRG_EINVAL = 1,    /* bad argument (NULL, out-of-range size, non-finite beta, ...) */
+    TRG_ESTATE = 2,    /* call out of order (e.g. coarse-grain before init) */
+    TRG_ENOMEM = 3,    /* allocation failed or exceeds the configured budget */
+    TRG_ENUMERIC = 4,  /* non-positive / NaN norm or trace, eigensolver not converged */
+    TRG_ETIMEOUT = 5,  /* a bounded device-side wait ran out */
+    TRG_ECUDA = 6,     /* a CUDA runtime call failed (see trg_last_error) */
+    TRG_ENOTSUP = 7    /* feature not available on this device / build */
+} trg_status;
+
+typedef enum trg_model { TRG_ISING = 0, TRG_XY = 1 } trg_model;
+
+/* Arithmetic of the contractions (environment, U.T.T.U, M.Q products).
+ * Cholesky-QR, the Rayleigh-Ritz eigensolve, normalisation and the log-norm
+ * accumulation are FP64 in every mode. */
+typedef enum trg_precision {
+    TRG_FP64 = 0,        /* plain FP64 on the CUDA cores */
+    TRG_SPLIT_BF16 = 1   /* FP64 operands cut into BF16 slices, exact FP32
+                            partial sums on tcgen05 tensor cores, summed wide */
+} trg_precision;
+
+typedef enum trg_trunc {
+    TRG_TRUNC_PAPER = 0,     /* keep min(Dx^2, Dcut) vectors, as the SVD helper does */
+    TRG_TRUNC_MULTIPLET = 1  /* lower Dn so the cut never splits a degenerate multiplet */
+} trg_trunc;
+
+typedef struct trg_config {
+    int precision;           /* trg_precision (default TRG_FP64) */
+    int split_slices;        /* BF16 slices per operand in TRG_SPLIT_BF16, 2..6 (default 4) */
+    int split_from_step;     /* half-steps with index < this run in FP64 (default 0) */
+    int trunc;               /* trg_trunc (default TRG_TRUNC_PAPER) */
+    double gap_tol;          /* multiplet gap, relative to lambda_1 (default 1e-8) */
+    int oversample;          /* subspace-iteration oversampling p (default 16) */
+    double eig_tol;          /* Ritz residual tolerance relative to lambda_1 (default 1e-12) */
+    int eig_max_iter;        /* subspace iterations before TRG_ENUMERIC (default 300) */
+    uint64_t seed;           /* seed of the start block of the subspace iteration */
+    size_t workspace_bytes;  /* bound on the contraction workspace (0 = 4 GiB) */
+} trg_config;
+
+typedef struct trg_ctx trg_ctx;
+
+/* Allocator hook: alloc returns device memory of `bytes` usable on `stream`
+ * (NULL on failure); free releases it.  `user` is passed back unchanged. */
+typedef void* (*trg_alloc_fn)(size_t bytes, void* stream, void* user);
+typedef void (*trg_free_fn)(void* ptr, size_t bytes, void* stream, void* user);
+
+/* Fill *cfg with the defaults listed above. */
+int trg_config_default(trg_config* cfg);
+
+/* Create a context on CUDA device `device`.  cfg may be NULL (defaults).
+ * Returns TRG_ENOTSUP if the device is not sm_103 (GB300). */
+int trg_create(trg_ctx** out, int device, const trg_config* cfg);
+
+/* Destroy a context and free all device memory it allocated. NULL is a no-op. */
+int trg_destroy(trg_ctx* ctx);
+
+/* Order all later device work of ctx on `stream` (a cudaStream_t). */
+int trg_set_stream(trg_ctx* ctx, void* stream);
+
+/* Route the context's device allocations through alloc/free.  Must be
+ * called before the first allocation (right after trg_create). */
+int trg_set_allocator(trg_ctx* ctx, trg_alloc_fn alloc, trg_free_fn free_fn, void* user);
+
+/* Change the precision mode for later half-steps (see trg_config). */
+int trg_set_precision(trg_ctx* ctx, int precision, int split_slices, int split_from_step);
+
+/* -------------------------------------------------------- full solve ---- */
+/*
+ * Build the initial site tensor T0 on the device and reset the solve.
+ *   TRG_ISING: D0 must be 2.  T[i,j,k,l] = sum_s e^{beta h s} W_si W_sj W_sk W_sl
+ *              with W the symmetric square root of B_ss' = e^{beta s s'}
+ *              (H = -sum s s' - h sum s).
+ *   TRG_XY:    D0 odd (charges |n| <= (D0-1)/2);
+ *              T = prod_legs sqrt(I_n(beta)) * I_{n_l+n_u-n_r-n_d}(beta h).
+ * beta must be > 0 and finite, h finite.  T0 is divided by n0 = max|T0|.
+ */
+int trg_init_tensor(trg_ctx* ctx, int model, double beta, double h, int D0);
+
+/* Same, from a caller tensor (host, shape (Dx,Dy,Dx,Dy), copied). */
+int trg_init_tensor_raw(trg_ctx* ctx, const double* T_host, int Dx, int Dy, double beta);
+
+/*
+ * Run `nsteps` directional blockings (half-steps), continuing the x/y
+ * alternation of earlier calls (x first).  Each half-step: environment M of
+ * two stacked tensors, isometry U = leading min(Dx^2, Dcut) eigenvectors of M,
+ * Tx = U.T.T.U, then T /= n_k = max|T| and lognorm += 2^-k ln n_k.
+ * Dcut >= 1.  Returns TRG_ENUMERIC on a non-positive or NaN norm, or if the
+ * eigensolver does not converge.
+ */
+int trg_coarse_grain(trg_ctx* ctx, int Dcut, int nsteps);
+
+/*
+ * Close the current tensor with periodic boundary conditions and return
+ * f = -(ln Z / V) / beta and (if lnz_per_site != NULL) ln Z / V, where
+ * ln Z / V = ln n0 + sum_k 2^-k ln n_k + 2^-N ln Tr T_N, Tr T = sum_ij T[i,j,i,j]
+ * (Sec. 2 and Fig. 1 for the trace, Sec. 3.2 for f = -T ln Z).
+ */
+int trg_free_energy(trg_ctx* ctx, double* f_out, double* lnz_per_site);
+
+/* Kept eigenvalues of M at half-step `step` (1-based), descending, written
+ * to out[0..min(cap,n)-1]; *n_out = number kept.  Untruncated steps (U = I)
+ * report n_out = 0. */
+int trg_get_spectrum(trg_ctx* ctx, int step, double* out, int cap, int* n_out);
+
+/* Current solve state: half-steps done, (Dx, Dy), and sum_k 2^-k ln n_k. */
+int trg_get_state(trg_ctx* ctx, int* steps, int* Dx, int* Dy, double* lognorm);
+
+/* Copy the current (normalised) tensor to host memory of cap doubles. */
+int trg_get_tensor(trg_ctx* ctx, double* T_host, size_t cap);
+
+/* ------------------------------------------- components (device buffers) */
+/*
+ * Environment of the x half-step (Sec. 2, the environment einsum of the
+ * coarse-graining listing):
+ *   M[(i,j),(k,l)] = sum t[j,a,b,e] t[i,e,c,d] t[l,a,b,f] t[k,f,c,d],
+ * t: device, (Dx,Dy,Dx,Dy) row-major; M: device, (Dx*Dx) x (Dx*Dx) row-major.
+ * Uses the context's precision mode and workspace.
+ */
+int trg_environment(trg_ctx* ctx, const double* t_dev, int Dx, int Dy, double* M_dev);
+
+/*
+ * Isometry from a symmetric PSD environment (the SVD helper of the listing:
+ * leading Dn = min(n, Dcut) left singular vectors of M, n = Dx*Dx; with
+ * TRG_TRUNC_MULTIPLET Dn may be lower).  M_dev: device, n x n row-major.
+ * U_dev: device, n x Dn row-major (capacity n*min(n,Dcut) doubles);
+ * lam_host: host, capacity min(n,Dcut) (nullable); *dn_out = Dn.
+ * If Dn == n the identity is returned and lam is not computed (*dn_out = n,
+ * lam_host untouched).
+ */
+int trg_isometry(trg_ctx* ctx, const double* M_dev, int n, int Dcut,
+                 double* U_dev, double* lam_host, int* dn_out);
+
+/*
+ * Contraction of the x half-step (Sec. 2, the U.T.T.U einsum):
+ *   Tx[i,j,k,l] = sum U[a,b,i] t[b,j,d,c] t[a,c,e,l] U[e,d,k],
+ * t: device (Dx,Dy,Dx,Dy); U: device (Dx,Dx,Dn); Tx: device (Dn,Dy,Dn,Dy).
+ * The D^5 intermediates are never formed whole: the free index j is
+ * processed in slices sized to the workspace bound.
+ */
+int trg_contract(trg_ctx* ctx, const double* t_dev, const double* U_dev,
+                 int Dx, int Dy, int Dn, double* Tx_dev);
+
+/* ------------------------------------------------------- profiling ----- */
+/* Phases of a half-step, timed with CUDA events on the context's stream. */
+typedef enum trg_phase {
+    TRG_PHASE_ENV = 0,    /* environment products (P, Q, M) */
+    TRG_PHASE_EIG = 1,    /* isometry: subspace iteration + Cholesky-QR + Rayleigh-Ritz */
+    TRG_PHASE_X1 = 2,     /* X1 = U.t        (D^6) */
+    TRG_PHASE_X2 = 3,     /* X2 = X1.t       (D^7, the dominant product) */
+    TRG_PHASE_X3 = 4,     /* Tx = X2.U       (D^6) */
+    TRG_PHASE_NORM = 5,   /* max-abs normalisation and log-norm */
+    TRG_PHASE_MMA = 6,    /* split mode: the tensor-core kernels alone (all products) */
+    TRG_PHASE_COUNT = 7
+} trg_phase;
+
+typedef struct trg_phase_stats {
+    double ms;          /* summed event time of the phase's timed regions */
+    uint64_t calls;     /* timed regions (one per product / normalisation) */
+    double flops;       /* algorithmic FLOPs: 2*M*N*K per product, FP64-equivalent */
+    double mma_flops;   /* tensor-core FLOPs issued (split mode: slice products x 2MNK) */
+} trg_phase_stats;
+
+/* Enable (on != 0) or disable phase timing; enabling resets the counters.
+ * Timing inserts event records around every product; it adds no sync. */
+int trg_profile_enable(trg_ctx* ctx, int on);
+
+/* Synchronise the stream and read the accumulated statistics of a phase. */
+int trg_profile_read(trg_ctx* ctx, int phase, trg_phase_stats* out);
+
+/* ------------------------------------------------------------ misc ----- */
+const char* trg_status_string(int status);
+const char* trg_last_error(const trg_ctx* ctx);
+/* Number of the library's own kernel launches issued by this context. */
+uint64_t trg_launch_count(const trg_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TRG_H */

@@ -106,12 +106,17 @@ def contract_x(t: np.ndarray, u: np.ndarray, j_chunk: int | None = None) -> np.n
         j_chunk = max(1, min(dy, int(2 ** 27 // max(1, dx * dx * dn * dy))))
     for j0 in range(0, dy, j_chunk):
         j1 = min(dy, j0 + j_chunk)
-        tj = t[:, j0:j1]                                   # (b, j, d, c)
-        x1 = np.tensordot(u, tj, axes=([1], [0]))          # (a, i, j, d, c)
-        x2 = np.tensordot(x1, t, axes=([0, 4], [0, 1]))    # (i, j, d, e, l)
-        x3 = np.tensordot(x2, u, axes=([2, 3], [1, 0]))    # (i, j, l, k)
-        out[:, j0:j1] = x3.transpose(0, 1, 3, 2)
+        out[:, j0:j1] = contract_x_slice(t, u, j0, j1)
     return out
+
+
+def contract_x_slice(t: np.ndarray, u: np.ndarray, j0: int, j1: int) -> np.ndarray:
+    """Tx[:, j0:j1, :, :] of contract_x."""
+    tj = t[:, j0:j1]                                   # (b, j, d, c)
+    x1 = np.tensordot(u, tj, axes=([1], [0]))          # (a, i, j, d, c)
+    x2 = np.tensordot(x1, t, axes=([0, 4], [0, 1]))    # (i, j, d, e, l)
+    x3 = np.tensordot(x2, u, axes=([2, 3], [1, 0]))    # (i, j, l, k)
+    return x3.transpose(0, 1, 3, 2)
 
 
 def rotate_in(t: np.ndarray) -> np.ndarray:

@@ -1,0 +1,539 @@
+// The C ABI of libtrg (include/trg.h): context, solve state machine and the
+// half-step driver (Sec. 2 and Fig. 1 of the paper: x half-step, y half-step
+// as the x half-step of the rotated tensor, normalisation, periodic trace).
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <stdexcept>
+
+#include "internal.h"
+
+namespace trg {
+
+[[noreturn]] void fail(int status, const std::string& msg) { throw Error{status, msg}; }
+
+void check_cuda(cudaError_t e, const char* what, const char* file, int line) {
+    if (e == cudaSuccess) return;
+    const char* base = std::strrchr(file, '/');
+    std::string m = std::string(what) + ": " + cudaGetErrorString(e) + " (" + (base ? base + 1 : file) + ":" +
+                    std::to_string(line) + ")";
+    if (e == cudaErrorMemoryAllocation) throw Error{TRG_ENOMEM, m};
+    throw Error{TRG_ECUDA, m};
+}
+
+void* Ctx::raw_alloc(size_t bytes) {
+    void* p = nullptr;
+    if (alloc_fn) {
+        p = alloc_fn(bytes, (void*)stream, alloc_user);
+        if (!p) fail(TRG_ENOMEM, "allocator hook returned NULL for " + std::to_string(bytes) + " bytes");
+    } else {
+        cudaError_t e = cudaMalloc(&p, bytes);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            fail(TRG_ENOMEM, "cudaMalloc(" + std::to_string(bytes) + "): " + cudaGetErrorString(e));
+        }
+    }
+    return p;
+}
+
+void Ctx::raw_free(void* p, size_t bytes) {
+    if (!p) return;
+    if (free_fn) free_fn(p, bytes, (void*)stream, alloc_user);
+    else cudaFree(p);
+}
+
+void Ctx::ensure(Buf& b, size_t bytes) {
+    if (b.bytes >= bytes && b.p) return;
+    if (b.p) {
+        // the old buffer may still be read by queued work
+        TRG_CUDA(cudaStreamSynchronize(stream));
+        raw_free(b.p, b.bytes);
+        b.p = nullptr;
+        b.bytes = 0;
+    }
+    const size_t sz = std::max<size_t>(bytes, 256);
+    b.p = raw_alloc(sz);
+    b.bytes = sz;
+}
+
+void Ctx::release(Buf& b) {
+    raw_free(b.p, b.bytes);
+    b.p = nullptr;
+    b.bytes = 0;
+}
+
+cudaEvent_t Ctx::get_event() {
+    if (!event_pool.empty()) {
+        cudaEvent_t e = event_pool.back();
+        event_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e;
+    TRG_CUDA(cudaEventCreate(&e));
+    return e;
+}
+
+int Ctx::region_begin(int p) {
+    if (!prof) return -1;
+    cudaEvent_t a = get_event(), b = get_event();
+    TRG_CUDA(cudaEventRecord(a, stream));
+    ph[p].pending.emplace_back(a, b);
+    return p;
+}
+
+void Ctx::region_end(int token, double flops, double mma_flops) {
+    if (token < 0) return;
+    TRG_CUDA(cudaEventRecord(ph[token].pending.back().second, stream));
+    ph[token].calls += 1;
+    ph[token].flops += flops;
+    ph[token].mma_flops += mma_flops;
+}
+
+void Ctx::collect_timings() {
+    TRG_CUDA(cudaStreamSynchronize(stream));
+    for (auto& acc : ph) {
+        for (auto& pr : acc.pending) {
+            float ms = 0.f;
+            TRG_CUDA(cudaEventElapsedTime(&ms, pr.first, pr.second));
+            acc.ms += ms;
+            event_pool.push_back(pr.first);
+            event_pool.push_back(pr.second);
+        }
+        acc.pending.clear();
+    }
+}
+
+static View4 contiguous_view(double* p, int64_t n0, int64_t n1, int64_t n2, int64_t n3) {
+    View4 v;
+    v.p = p;
+    v.n[0] = n0; v.n[1] = n1; v.n[2] = n2; v.n[3] = n3;
+    v.s[3] = 1; v.s[2] = n3; v.s[1] = n2 * n3; v.s[0] = n1 * n2 * n3;
+    return v;
+}
+
+// One directional blocking.  Step k (1-based): odd = x, even = y.
+static void half_step(Ctx& ctx, int dcut) {
+    const int k = ctx.steps + 1;
+    const bool xdir = (k % 2) == 1;
+    const int64_t Dx = ctx.Dx, Dy = ctx.Dy;
+    const int precision = precision_for_step(ctx, k);
+    View4 t = contiguous_view(ctx.T.as<double>(), Dx, Dy, Dx, Dy);
+    View4 r = t;   // the tensor the x formulas see
+    if (!xdir) {
+        // R = permute(T, (1, 2, 3, 0)): R[p0,p1,p2,p3] = T[p3,p0,p1,p2]
+        r.n[0] = t.n[1]; r.n[1] = t.n[2]; r.n[2] = t.n[3]; r.n[3] = t.n[0];
+        r.s[0] = t.s[1]; r.s[1] = t.s[2]; r.s[2] = t.s[3]; r.s[3] = t.s[0];
+    }
+    const int64_t rx = r.n[0], ry = r.n[1];
+    const int64_t n = rx * rx;
+    const int64_t dn_max = std::min<int64_t>(n, dcut);
+
+    ctx.ensure(ctx.M, (size_t)(n * n) * sizeof(double));
+    ctx.ensure(ctx.U, (size_t)(n * dn_max) * sizeof(double));
+    ctx.phase = TRG_PHASE_ENV;
+    environment(ctx, r, ctx.M.as<double>(), precision);
+
+    std::vector<double> lam;
+    int64_t dn = dn_max;
+    ctx.phase = TRG_PHASE_EIG;
+    {
+        const int tok = ctx.region_begin(TRG_PHASE_EIG);
+        if (dn_max == n) {
+            launch_identity(ctx, ctx.U.as<double>(), n);
+        } else {
+            dn = isometry(ctx, ctx.M.as<double>(), n, dcut, ctx.U.as<double>(), lam, k, precision);
+        }
+        ctx.region_end(tok, 0.0, 0.0);
+    }
+
+    // output O (dn, ry, dn, ry) of the x formulas
+    View4 out;
+    int64_t newDx, newDy;
+    if (xdir) {
+        newDx = dn; newDy = Dy;
+        ctx.ensure(ctx.Tnext, (size_t)(dn * Dy * dn * Dy) * sizeof(double));
+        out = contiguous_view(ctx.Tnext.as<double>(), dn, Dy, dn, Dy);
+    } else {
+        // Txy = permute(O, (3, 0, 1, 2)) has shape (ry, dn, ry, dn) = (Dx, dn, Dx, dn)
+        newDx = Dx; newDy = dn;
+        ctx.ensure(ctx.Tnext, (size_t)(Dx * dn * Dx * dn) * sizeof(double));
+        View4 txy = contiguous_view(ctx.Tnext.as<double>(), Dx, dn, Dx, dn);
+        out.p = txy.p;
+        out.n[0] = dn; out.n[1] = ry; out.n[2] = dn; out.n[3] = ry;
+        out.s[0] = txy.s[1]; out.s[1] = txy.s[2]; out.s[2] = txy.s[3]; out.s[3] = txy.s[0];
+    }
+    contract(ctx, r, ctx.U.as<double>(), dn, out, precision);
+    {
+        const int tok = ctx.region_begin(TRG_PHASE_NORM);
+        launch_normalise(ctx, ctx.Tnext.as<double>(), newDx * newDy * newDx * newDy, k, false);
+        ctx.region_end(tok, 0.0, 0.0);
+    }
+    const int st = read_status(ctx);
+    if (st & ST_BAD_NORM) fail(TRG_ENUMERIC, "non-positive or non-finite norm at half-step " + std::to_string(k));
+    std::swap(ctx.T, ctx.Tnext);
+    ctx.Dx = (int)newDx;
+    ctx.Dy = (int)newDy;
+    ctx.steps = k;
+    ctx.spectra.push_back(lam);
+}
+
+static void reset_solve(Ctx& ctx) {
+    ctx.have_tensor = false;
+    ctx.steps = 0;
+    ctx.spectra.clear();
+    TRG_CUDA(cudaMemsetAsync(ctx.scal.p, 0, SC_COUNT * sizeof(double), ctx.stream));
+    TRG_CUDA(cudaMemsetAsync(ctx.status.p, 0, sizeof(int), ctx.stream));
+}
+
+static void finish_init(Ctx& ctx, int Dx, int Dy, double beta) {
+    launch_normalise(ctx, ctx.T.as<double>(), (int64_t)Dx * Dy * Dx * Dy, 0, true);
+    const int st = read_status(ctx);
+    if (st & ST_BAD_NORM) fail(TRG_ENUMERIC, "initial tensor has no positive norm");
+    ctx.Dx = Dx;
+    ctx.Dy = Dy;
+    ctx.beta = beta;
+    ctx.have_tensor = true;
+}
+
+}  // namespace trg
+
+using trg::Ctx;
+using trg::Error;
+
+struct trg_ctx : public Ctx {};
+
+#define TRG_GUARD_BEGIN try {
+#define TRG_GUARD_END(ctxp)                                                      \
+    }                                                                            \
+    catch (const Error& e) {                                                     \
+        if (ctxp) (ctxp)->last_error = e.msg;                                    \
+        return e.status;                                                         \
+    }                                                                            \
+    catch (const std::bad_alloc&) {                                              \
+        if (ctxp) (ctxp)->last_error = "host allocation failed";                \
+        return TRG_ENOMEM;                                                       \
+    }                                                                            \
+    catch (const std::exception& e) {                                            \
+        if (ctxp) (ctxp)->last_error = e.what();                                 \
+        return TRG_ECUDA;                                                        \
+    }
+
+static int bad(trg_ctx* ctx, int status, const char* msg) {
+    if (ctx) ctx->last_error = msg;
+    return status;
+}
+
+extern "C" {
+
+int trg_config_default(trg_config* cfg) {
+    if (!cfg) return TRG_EINVAL;
+    std::memset(cfg, 0, sizeof(*cfg));
+    cfg->precision = TRG_FP64;
+    cfg->split_slices = 4;
+    cfg->split_from_step = 0;
+    cfg->trunc = TRG_TRUNC_PAPER;
+    cfg->gap_tol = 1e-8;
+    cfg->oversample = 16;
+    cfg->eig_tol = 1e-12;
+    cfg->eig_max_iter = 300;
+    cfg->seed = 0x5EEDull;
+    cfg->workspace_bytes = 0;
+    return TRG_OK;
+}
+
+static int validate_config(const trg_config& c) {
+    if (c.precision != TRG_FP64 && c.precision != TRG_SPLIT_BF16) return TRG_EINVAL;
+    if (c.split_slices < 2 || c.split_slices > 6) return TRG_EINVAL;
+    if (c.split_from_step < 0) return TRG_EINVAL;
+    if (c.trunc != TRG_TRUNC_PAPER && c.trunc != TRG_TRUNC_MULTIPLET) return TRG_EINVAL;
+    if (!(c.gap_tol >= 0.0) || !(c.eig_tol > 0.0) || c.oversample < 1 || c.eig_max_iter < 1) return TRG_EINVAL;
+    return TRG_OK;
+}
+
+int trg_create(trg_ctx** out, int device, const trg_config* cfg) {
+    if (!out) return TRG_EINVAL;
+    *out = nullptr;
+    trg_ctx* ctx = new (std::nothrow) trg_ctx();
+    if (!ctx) return TRG_ENOMEM;
+    TRG_GUARD_BEGIN
+    if (cfg) ctx->cfg = *cfg;
+    else trg_config_default(&ctx->cfg);
+    if (validate_config(ctx->cfg) != TRG_OK) { delete ctx; return TRG_EINVAL; }
+    int ndev = 0;
+    TRG_CUDA(cudaGetDeviceCount(&ndev));
+    if (device < 0 || device >= ndev) { delete ctx; return TRG_EINVAL; }
+    TRG_CUDA(cudaSetDevice(device));
+    cudaDeviceProp prop;
+    TRG_CUDA(cudaGetDeviceProperties(&prop, device));
+    if (prop.major != 10 || prop.minor != 3) {
+        delete ctx;
+        return TRG_ENOTSUP;
+    }
+    ctx->device = device;
+    ctx->sm_count = prop.multiProcessorCount;
+    ctx->stream = nullptr;
+    ctx->ensure(ctx->scal, trg::SC_COUNT * sizeof(double));
+    ctx->ensure(ctx->status, 64);
+    TRG_CUDA(cudaMemset(ctx->scal.p, 0, trg::SC_COUNT * sizeof(double)));
+    TRG_CUDA(cudaMemset(ctx->status.p, 0, 64));
+    *out = ctx;
+    return TRG_OK;
+    }
+    catch (const Error& e) {
+        int st = e.status;
+        delete ctx;
+        return st;
+    }
+}
+
+int trg_destroy(trg_ctx* ctx) {
+    if (!ctx) return TRG_OK;
+    cudaSetDevice(ctx->device);
+    cudaStreamSynchronize(ctx->stream);
+    Ctx& c = *ctx;
+    for (trg::Buf* b : {&c.T, &c.Tnext, &c.M, &c.U, &c.scal, &c.status, &c.ws, &c.envP, &c.envQ, &c.eig,
+                        &c.eig_small, &c.flags})
+        c.release(*b);
+    for (auto& kv : c.tables) c.release(kv.second);
+    c.tables.clear();
+    c.collect_timings();
+    for (cudaEvent_t e : c.event_pool) cudaEventDestroy(e);
+    delete ctx;
+    return TRG_OK;
+}
+
+int trg_set_stream(trg_ctx* ctx, void* stream) {
+    if (!ctx) return TRG_EINVAL;
+    ctx->stream = (cudaStream_t)stream;
+    return TRG_OK;
+}
+
+int trg_set_allocator(trg_ctx* ctx, trg_alloc_fn alloc, trg_free_fn free_fn, void* user) {
+    if (!ctx || (!alloc) != (!free_fn)) return TRG_EINVAL;
+    // only the two always-present scalar buffers exist at this point: move them
+    if (ctx->T.p || ctx->M.p || !ctx->tables.empty())
+        return bad(ctx, TRG_ESTATE, "trg_set_allocator must come before any other call");
+    TRG_GUARD_BEGIN
+    TRG_CUDA(cudaStreamSynchronize(ctx->stream));
+    ctx->release(ctx->scal);
+    ctx->release(ctx->status);
+    ctx->alloc_fn = alloc;
+    ctx->free_fn = free_fn;
+    ctx->alloc_user = user;
+    ctx->ensure(ctx->scal, trg::SC_COUNT * sizeof(double));
+    ctx->ensure(ctx->status, 64);
+    TRG_CUDA(cudaMemsetAsync(ctx->scal.p, 0, trg::SC_COUNT * sizeof(double), ctx->stream));
+    TRG_CUDA(cudaMemsetAsync(ctx->status.p, 0, 64, ctx->stream));
+    return TRG_OK;
+    TRG_GUARD_END(ctx)
+}
+
+int trg_set_precision(trg_ctx* ctx, int precision, int split_slices, int split_from_step) {
+    if (!ctx) return TRG_EINVAL;
+    trg_config c = ctx->cfg;
+    c.precision = precision;
+    c.split_slices = split_slices;
+    c.split_from_step = split_from_step;
+    if (validate_config(c) != TRG_OK) return bad(ctx, TRG_EINVAL, "invalid precision settings");
+    ctx->cfg = c;
+    return TRG_OK;
+}
+
+int trg_init_tensor(trg_ctx* ctx, int model, double beta, double h, int D0) {
+    if (!ctx) return TRG_EINVAL;
+    if (!(beta > 0.0) || !std::isfinite(beta) || !std::isfinite(h))
+        return bad(ctx, TRG_EINVAL, "beta must be positive and finite, h finite");
+    TRG_GUARD_BEGIN
+    TRG_CUDA(cudaSetDevice(ctx->device));
+    if (model == TRG_ISING) {
+        if (D0 != 2) return bad(ctx, TRG_EINVAL, "Ising: D0 must be 2");
+        trg::reset_solve(*ctx);
+        ctx->ensure(ctx->T, 16 * sizeof(double));
+        trg::launch_init_ising(*ctx, ctx->T.as<double>(), beta, h);
+        trg::finish_init(*ctx, 2, 2, beta);
+    } else if (model == TRG_XY) {
+        if (D0 < 1 || D0 % 2 == 0 || D0 > 41) return bad(ctx, TRG_EINVAL, "XY: D0 must be odd, 1..41");
+        trg::reset_solve(*ctx);
+        const size_t n = (size_t)D0 * D0 * D0 * D0;
+        ctx->ensure(ctx->T, n * sizeof(double));
+        trg::launch_init_xy(*ctx, ctx->T.as<double>(), D0, beta, h);
+        trg::finish_init(*ctx, D0, D0, beta);
+    } else {
+        return bad(ctx, TRG_EINVAL, "unknown model");
+    }
+    return TRG_OK;
+    TRG_GUARD_END(ctx)
+}
+
+int trg_init_tensor_raw(trg_ctx* ctx, const double* T_host, int Dx, int Dy, double beta) {
+    if (!ctx) return TRG_EINVAL;
+    if (!T_host || Dx < 1 || Dy < 1 || Dx > 4096 || Dy > 4096)
+        return bad(ctx, TRG_EINVAL, "init_tensor_raw: bad tensor");
+    if (!(beta > 0.0) || !std::isfinite(beta)) return bad(ctx, TRG_EINVAL, "beta must be positive and finite");
+    TRG_GUARD_BEGIN
+    TRG_CUDA(cudaSetDevice(ctx->device));
+    trg::reset_solve(*ctx);
+    const size_t n = (size_t)Dx * Dy * Dx * Dy;
+    ctx->ensure(ctx->T, n * sizeof(double));
+    TRG_CUDA(cudaMemcpyAsync(ctx->T.p, T_host, n * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+    trg::finish_init(*ctx, Dx, Dy, beta);
+    return TRG_OK;
+    TRG_GUARD_END(ctx)
+}
+
+int trg_coarse_grain(trg_ctx* ctx, int Dcut, int nsteps) {
+    if (!ctx) return TRG_EINVAL;
+    if (!ctx->have_tensor) return bad(ctx, TRG_ESTATE, "coarse_grain before init_tensor");
+    if (Dcut < 1 || nsteps < 0) return bad(ctx, TRG_EINVAL, "Dcut >= 1 and nsteps >= 0 required");
+    if (ctx->steps + nsteps > 1000) return bad(ctx, TRG_EINVAL, "more than 1000 half-steps");
+    TRG_GUARD_BEGIN
+    TRG_CUDA(cudaSetDevice(ctx->device));
+    for (int i = 0; i < nsteps; ++i) trg::half_step(*ctx, Dcut);
+    return TRG_OK;
+    TRG_GUARD_END(ctx)
+}
+
+int trg_free_energy(trg_ctx* ctx, double* f_out, double* lnz_per_site) {
+    if (!ctx) return TRG_EINVAL;
+    if (!ctx->have_tensor) return bad(ctx, TRG_ESTATE, "free_energy before init_tensor");
+    if (!f_out && !lnz_per_site) return bad(ctx, TRG_EINVAL, "no output");
+    TRG_GUARD_BEGIN
+    TRG_CUDA(cudaSetDevice(ctx->device));
+    double* scal = ctx->scal.as<double>();
+    trg::launch_trace(*ctx, ctx->T.as<double>(), ctx->Dx, ctx->Dy, scal + trg::SC_TRACE);
+    double h[trg::SC_COUNT];
+    TRG_CUDA(cudaMemcpyAsync(h, scal, sizeof(h), cudaMemcpyDeviceToHost, ctx->stream));
+    TRG_CUDA(cudaStreamSynchronize(ctx->stream));
+    if (trg::read_status(*ctx) & trg::ST_BAD_TRACE) return bad(ctx, TRG_ENUMERIC, "non-positive trace");
+    const double lnz = h[trg::SC_LN_N0] + h[trg::SC_LOGNORM] + std::ldexp(std::log(h[trg::SC_TRACE]), -ctx->steps);
+    if (lnz_per_site) *lnz_per_site = lnz;
+    if (f_out) *f_out = -lnz / ctx->beta;
+    return TRG_OK;
+    TRG_GUARD_END(ctx)
+}
+
+int trg_get_spectrum(trg_ctx* ctx, int step, double* out, int cap, int* n_out) {
+    if (!ctx || !n_out) return TRG_EINVAL;
+    if (step < 1 || step > (int)ctx->spectra.size()) return bad(ctx, TRG_EINVAL, "no such half-step");
+    const std::vector<double>& s = ctx->spectra[(size_t)step - 1];
+    *n_out = (int)s.size();
+    if (out && cap > 0) std::memcpy(out, s.data(), sizeof(double) * (size_t)std::min<int>(cap, (int)s.size()));
+    return TRG_OK;
+}
+
+int trg_get_state(trg_ctx* ctx, int* steps, int* Dx, int* Dy, double* lognorm) {
+    if (!ctx) return TRG_EINVAL;
+    TRG_GUARD_BEGIN
+    if (steps) *steps = ctx->steps;
+    if (Dx) *Dx = ctx->Dx;
+    if (Dy) *Dy = ctx->Dy;
+    if (lognorm) {
+        TRG_CUDA(cudaMemcpyAsync(lognorm, ctx->scal.as<double>() + trg::SC_LOGNORM, sizeof(double),
+                                 cudaMemcpyDeviceToHost, ctx->stream));
+        TRG_CUDA(cudaStreamSynchronize(ctx->stream));
+    }
+    return TRG_OK;
+    TRG_GUARD_END(ctx)
+}
+
+int trg_get_tensor(trg_ctx* ctx, double* T_host, size_t cap) {
+    if (!ctx || !T_host) return TRG_EINVAL;
+    if (!ctx->have_tensor) return bad(ctx, TRG_ESTATE, "no tensor");
+    const size_t n = (size_t)ctx->Dx * ctx->Dy * ctx->Dx * ctx->Dy;
+    if (cap < n) return bad(ctx, TRG_EINVAL, "buffer too small");
+    TRG_GUARD_BEGIN
+    TRG_CUDA(cudaMemcpyAsync(T_host, ctx->T.p, n * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    TRG_CUDA(cudaStreamSynchronize(ctx->stream));
+    return TRG_OK;
+    TRG_GUARD_END(ctx)
+}
+
+int trg_environment(trg_ctx* ctx, const double* t_dev, int Dx, int Dy, double* M_dev) {
+    if (!ctx) return TRG_EINVAL;
+    if (!t_dev || !M_dev || Dx < 1 || Dy < 1) return bad(ctx, TRG_EINVAL, "environment: bad arguments");
+    TRG_GUARD_BEGIN
+    TRG_CUDA(cudaSetDevice(ctx->device));
+    trg::View4 t = trg::contiguous_view(const_cast<double*>(t_dev), Dx, Dy, Dx, Dy);
+    trg::environment(*ctx, t, M_dev, ctx->cfg.precision);
+    TRG_CUDA(cudaStreamSynchronize(ctx->stream));
+    return TRG_OK;
+    TRG_GUARD_END(ctx)
+}
+
+int trg_isometry(trg_ctx* ctx, const double* M_dev, int n, int Dcut, double* U_dev, double* lam_host, int* dn_out) {
+    if (!ctx) return TRG_EINVAL;
+    if (!M_dev || !U_dev || !dn_out || n < 1 || Dcut < 1) return bad(ctx, TRG_EINVAL, "isometry: bad arguments");
+    TRG_GUARD_BEGIN
+    TRG_CUDA(cudaSetDevice(ctx->device));
+    const int dn_max = std::min(n, Dcut);
+    if (dn_max == n) {
+        trg::launch_identity(*ctx, U_dev, n);
+        *dn_out = n;
+    } else {
+        std::vector<double> lam;
+        const int dn = trg::isometry(*ctx, M_dev, n, Dcut, U_dev, lam, 1, ctx->cfg.precision);
+        *dn_out = dn;
+        if (lam_host) std::memcpy(lam_host, lam.data(), sizeof(double) * (size_t)dn);
+    }
+    TRG_CUDA(cudaStreamSynchronize(ctx->stream));
+    return TRG_OK;
+    TRG_GUARD_END(ctx)
+}
+
+int trg_contract(trg_ctx* ctx, const double* t_dev, const double* U_dev, int Dx, int Dy, int Dn, double* Tx_dev) {
+    if (!ctx) return TRG_EINVAL;
+    if (!t_dev || !U_dev || !Tx_dev || Dx < 1 || Dy < 1 || Dn < 1 || Dn > Dx * Dx)
+        return bad(ctx, TRG_EINVAL, "contract: bad arguments");
+    TRG_GUARD_BEGIN
+    TRG_CUDA(cudaSetDevice(ctx->device));
+    trg::View4 t = trg::contiguous_view(const_cast<double*>(t_dev), Dx, Dy, Dx, Dy);
+    trg::View4 o = trg::contiguous_view(Tx_dev, Dn, Dy, Dn, Dy);
+    trg::contract(*ctx, t, U_dev, Dn, o, ctx->cfg.precision);
+    TRG_CUDA(cudaStreamSynchronize(ctx->stream));
+    return TRG_OK;
+    TRG_GUARD_END(ctx)
+}
+
+int trg_profile_enable(trg_ctx* ctx, int on) {
+    if (!ctx) return TRG_EINVAL;
+    TRG_GUARD_BEGIN
+    ctx->collect_timings();
+    for (auto& acc : ctx->ph) { acc.ms = 0.0; acc.flops = 0.0; acc.mma_flops = 0.0; acc.calls = 0; }
+    ctx->prof = on != 0;
+    return TRG_OK;
+    TRG_GUARD_END(ctx)
+}
+
+int trg_profile_read(trg_ctx* ctx, int phase, trg_phase_stats* out) {
+    if (!ctx || !out || phase < 0 || phase >= TRG_PHASE_COUNT) return TRG_EINVAL;
+    TRG_GUARD_BEGIN
+    ctx->collect_timings();
+    const auto& a = ctx->ph[phase];
+    out->ms = a.ms;
+    out->calls = a.calls;
+    out->flops = a.flops;
+    out->mma_flops = a.mma_flops;
+    return TRG_OK;
+    TRG_GUARD_END(ctx)
+}
+
+const char* trg_status_string(int status) {
+    switch (status) {
+        case TRG_OK: return "ok";
+        case TRG_EINVAL: return "invalid argument";
+        case TRG_ESTATE: return "call out of order";
+        case TRG_ENOMEM: return "out of memory";
+        case TRG_ENUMERIC: return "numerical failure";
+        case TRG_ETIMEOUT: return "device wait timed out";
+        case TRG_ECUDA: return "CUDA error";
+        case TRG_ENOTSUP: return "not supported";
+        default: return "unknown status";
+    }
+}
+
+const char* trg_last_error(const trg_ctx* ctx) { return ctx ? ctx->last_error.c_str() : ""; }
+
+uint64_t trg_launch_count(const trg_ctx* ctx) { return ctx ? ctx->launches : 0; }
+
+}  // extern "C"

@@ -1,0 +1,414 @@
+// Isometry of the HOTRG step: leading eigenvectors of the environment M.
+//
+// The paper (Sec. 2, SVD helper of the coarse-graining listing) keeps the
+// leading min(n, Dcut) left singular vectors of M; M is a Gram matrix
+// (symmetric PSD), so these are its leading eigenvectors.  Here they come from
+// block subspace iteration:
+//   Y = M Q                                  (GEMM, the context's precision)
+//   H = Q^T Y, H = W diag(theta) W^T         (Rayleigh-Ritz, FP64 Jacobi)
+//   residual |Y w_i - theta_i Q w_i| <= tol * theta_1 for i < Dn  -> done
+//   Q <- orth(Y W)                           (FP64 Cholesky-QR, two passes)
+// Cholesky-QR works on column-normalised blocks; a column whose Cholesky
+// pivot shows it is numerically dependent on the earlier ones is replaced by
+// a fresh seeded random column (this happens when M's spectrum falls below
+// rounding, e.g. in the ordered phase).  All blocks are column-major (n x m).
+#include <algorithm>
+#include <cmath>
+
+#include "internal.h"
+
+namespace trg {
+
+namespace {
+
+constexpr int MAX_M = 112;   // largest block (Dcut + oversampling) held in shared memory
+
+__device__ __forceinline__ uint64_t splitmix64(uint64_t x) {
+    x += 0x9E3779B97F4A7C15ull;
+    x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
+    x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
+    return x ^ (x >> 31);
+}
+
+// Seeded uniform(-1, 1) entries; only columns with flags[c] != 0 when flags is given.
+__global__ void k_rand_cols(double* Y, int64_t n, int m, const int* flags, uint64_t seed, uint64_t salt) {
+    const int c = blockIdx.y;
+    if (c >= m || (flags && !flags[c])) return;
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x) {
+        uint64_t h = splitmix64(seed ^ splitmix64(salt * 0x100000001B3ull + (uint64_t)c * 0x9E3779B1ull + (uint64_t)r));
+        Y[(int64_t)c * n + r] = 2.0 * ((double)(h >> 11) * (1.0 / 9007199254740992.0)) - 1.0;
+    }
+}
+
+template <int NT>
+__device__ double block_sum(double v, double* red) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) red[w] = v;
+    __syncthreads();
+    double s = 0.0;
+    if (threadIdx.x < 32) {
+        s = (threadIdx.x < NT / 32) ? red[threadIdx.x] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (threadIdx.x == 0) red[0] = s;
+    }
+    __syncthreads();
+    return red[0];
+}
+
+// Scale every column to unit 2-norm; flag columns that are zero or not finite.
+__global__ void __launch_bounds__(256) k_col_normalize(double* Y, int64_t n, int* flags) {
+    __shared__ double red[32];
+    const int c = blockIdx.x;
+    double* y = Y + (int64_t)c * n;
+    double mx = 0.0;
+    for (int64_t r = threadIdx.x; r < n; r += 256) mx = fmax(mx, fabs(y[r]));
+    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double v = 0.0;
+        for (int i = 0; i < 8; ++i) v = fmax(v, red[i]);
+        red[8] = v;
+    }
+    __syncthreads();
+    mx = red[8];
+    __syncthreads();
+    if (!(mx > 0.0) || !isfinite(mx)) {
+        if (threadIdx.x == 0) flags[c] = 1;
+        return;
+    }
+    const double inv = 1.0 / mx;   // scale first so the squares cannot under/overflow
+    double s = 0.0;
+    for (int64_t r = threadIdx.x; r < n; r += 256) { const double v = y[r] * inv; s = fma(v, v, s); }
+    s = block_sum<256>(s, red);
+    const double scale = inv / sqrt(s);
+    for (int64_t r = threadIdx.x; r < n; r += 256) y[r] *= scale;
+}
+
+// Left-looking Cholesky G = L L^T of an m x m Gram matrix of unit columns.
+// A pivot d_j <= tau * G_jj marks column j as dependent (flags[j] = 1,
+// *nbad += 1); it is replaced by G_jj so the factorisation can continue.
+__global__ void __launch_bounds__(256) k_chol_flag(const double* G, double* Lout, int m, double tau,
+                                                   int* flags, int* nbad) {
+    extern __shared__ double L[];   // m*m, row-major
+    __shared__ double red[33];
+    for (int e = threadIdx.x; e < m * m; e += 256) L[e] = 0.0;
+    __syncthreads();
+    for (int j = 0; j < m; ++j) {
+        double part = 0.0;
+        for (int k = threadIdx.x; k < j; k += 256) part = fma(L[j * m + k], L[j * m + k], part);
+        const double sq = block_sum<256>(part, red);
+        const double gjj = G[(int64_t)j * m + j];
+        double d = gjj - sq;
+        if (!(d > tau * gjj) || !isfinite(d)) {
+            if (threadIdx.x == 0) { flags[j] = 1; atomicAdd(nbad, 1); }
+            d = (gjj > 0.0 && isfinite(gjj)) ? gjj : 1.0;
+        }
+        const double ljj = sqrt(d);
+        if (threadIdx.x == 0) L[j * m + j] = ljj;
+        __syncthreads();
+        for (int i = j + 1 + threadIdx.x; i < m; i += 256) {
+            double a = G[(int64_t)i * m + j];
+            for (int k = 0; k < j; ++k) a = fma(-L[i * m + k], L[j * m + k], a);
+            L[i * m + j] = a / ljj;
+        }
+        __syncthreads();
+    }
+    for (int e = threadIdx.x; e < m * m; e += 256) Lout[e] = L[e];
+}
+
+// Q = Y L^{-T} row by row (forward substitution), in place allowed.
+__global__ void __launch_bounds__(128) k_trsm_rows(double* Y, const double* Lg, int64_t n, int m) {
+    extern __shared__ double L[];
+    for (int e = threadIdx.x; e < m * m; e += blockDim.x) L[e] = Lg[e];
+    __syncthreads();
+    const int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (r >= n) return;
+    for (int j = 0; j < m; ++j) {
+        double a = Y[(int64_t)j * n + r];
+        for (int k = 0; k < j; ++k) a = fma(-L[j * m + k], Y[(int64_t)k * n + r], a);
+        Y[(int64_t)j * n + r] = a / L[j * m + j];
+    }
+}
+
+// Cyclic Jacobi with parallel (round-robin) ordering on a symmetric m x m
+// matrix held in shared memory.  Rotation (p,q): tau = (h_qq - h_pp)/(2 h_pq),
+// t = sign(tau)/(|tau| + sqrt(1+tau^2)), c = 1/sqrt(1+t^2), s = t c;
+// H <- J^T H J, W <- W J.  Rotations with |h_pq| <= tol sqrt(|h_pp h_qq|) are
+// skipped; a sweep without rotations ends the iteration.  Output: theta
+// sorted descending and W (column-major) with columns in the same order.
+__global__ void __launch_bounds__(512) k_jacobi(const double* Hg, int m, double tol, int max_sweeps,
+                                                double* theta, double* Wout, int* status) {
+    extern __shared__ double sm[];
+    const int mp = m + (m & 1);            // even player count (dummy index m when odd)
+    double* H = sm;                        // m*m row-major
+    double* cs = H + m * m;                // 2 per pair
+    int* rot = (int*)(cs + mp);            // rotations this sweep
+    int* perm = rot + 1;                   // m
+    for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
+        const int i = e / m, j = e % m;
+        H[e] = 0.5 * (Hg[(int64_t)i * m + j] + Hg[(int64_t)j * m + i]);
+        Wout[(int64_t)j * m + i] = (i == j) ? 1.0 : 0.0;   // W column-major
+    }
+    __syncthreads();
+    const int npair = mp / 2;
+    int sweep = 0;
+    for (; sweep < max_sweeps; ++sweep) {
+        if (threadIdx.x == 0) *rot = 0;
+        __syncthreads();
+        for (int r = 0; r < mp - 1; ++r) {
+            for (int i = threadIdx.x; i < npair; i += blockDim.x) {
+                int p, q;
+                if (i == 0) { p = mp - 1; q = r; }
+                else { p = (r + i) % (mp - 1); q = (r - i + (mp - 1)) % (mp - 1); }
+                if (p > q) { const int x = p; p = q; q = x; }
+                double c = 1.0, s = 0.0;
+                if (q < m) {
+                    const double hpq = H[p * m + q], hpp = H[p * m + p], hqq = H[q * m + q];
+                    if (fabs(hpq) > tol * sqrt(fabs(hpp * hqq)) && fabs(hpq) > 1e-300) {
+                        const double tau = (hqq - hpp) / (2.0 * hpq);
+                        const double t = (tau >= 0.0) ? 1.0 / (tau + sqrt(1.0 + tau * tau))
+                                                      : -1.0 / (-tau + sqrt(1.0 + tau * tau));
+                        c = 1.0 / sqrt(1.0 + t * t);
+                        s = t * c;
+                        atomicAdd(rot, 1);
+                    }
+                }
+                cs[2 * i] = c; cs[2 * i + 1] = s;
+            }
+            __syncthreads();
+            // columns: H <- H J, W <- W J
+            for (int e = threadIdx.x; e < npair * m; e += blockDim.x) {
+                const int i = e / m, k = e % m;
+                const double s = cs[2 * i + 1];
+                if (s == 0.0) continue;
+                const double c = cs[2 * i];
+                int p, q;
+                if (i == 0) { p = mp - 1; q = r; }
+                else { p = (r + i) % (mp - 1); q = (r - i + (mp - 1)) % (mp - 1); }
+                if (p > q) { const int x = p; p = q; q = x; }
+                const double hkp = H[k * m + p], hkq = H[k * m + q];
+                H[k * m + p] = c * hkp - s * hkq;
+                H[k * m + q] = s * hkp + c * hkq;
+                double* wp = Wout + (int64_t)p * m;
+                double* wq = Wout + (int64_t)q * m;
+                const double vp = wp[k], vq = wq[k];
+                wp[k] = c * vp - s * vq;
+                wq[k] = s * vp + c * vq;
+            }
+            __syncthreads();
+            // rows: H <- J^T H
+            for (int e = threadIdx.x; e < npair * m; e += blockDim.x) {
+                const int i = e / m, k = e % m;
+                const double s = cs[2 * i + 1];
+                if (s == 0.0) continue;
+                const double c = cs[2 * i];
+                int p, q;
+                if (i == 0) { p = mp - 1; q = r; }
+                else { p = (r + i) % (mp - 1); q = (r - i + (mp - 1)) % (mp - 1); }
+                if (p > q) { const int x = p; p = q; q = x; }
+                const double hpk = H[p * m + k], hqk = H[q * m + k];
+                H[p * m + k] = c * hpk - s * hqk;
+                H[q * m + k] = s * hpk + c * hqk;
+            }
+            __syncthreads();
+            for (int i = threadIdx.x; i < npair; i += blockDim.x) {
+                if (cs[2 * i + 1] == 0.0) continue;
+                int p, q;
+                if (i == 0) { p = mp - 1; q = r; }
+                else { p = (r + i) % (mp - 1); q = (r - i + (mp - 1)) % (mp - 1); }
+                if (p > q) { const int x = p; p = q; q = x; }
+                H[p * m + q] = 0.0;
+                H[q * m + p] = 0.0;
+            }
+            __syncthreads();
+        }
+        const int nrot = *rot;
+        __syncthreads();
+        if (nrot == 0) break;
+    }
+    if (threadIdx.x == 0) {
+        if (sweep >= max_sweeps) atomicOr(status, ST_EIG_NOCONV);
+        // selection order, descending (stable for ties)
+        for (int i = 0; i < m; ++i) perm[i] = i;
+        for (int i = 0; i < m; ++i) {
+            int best = i;
+            for (int j = i + 1; j < m; ++j)
+                if (H[perm[j] * m + perm[j]] > H[perm[best] * m + perm[best]]) best = j;
+            const int x = perm[i]; perm[i] = perm[best]; perm[best] = x;
+        }
+        for (int i = 0; i < m; ++i) theta[i] = H[perm[i] * m + perm[i]];
+    }
+    __syncthreads();
+    // permute W's columns into the sorted order (via H's storage, now free)
+    for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
+        const int col = e / m, row = e % m;
+        H[e] = Wout[(int64_t)perm[col] * m + row];
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < m * m; e += blockDim.x) Wout[e] = H[e];
+}
+
+// max_i<dn |Z_i - theta_i QW_i| / theta_0, as bits of a non-negative double.
+__global__ void __launch_bounds__(256) k_residual(const double* Z, const double* QW, const double* theta,
+                                                  int64_t n, unsigned long long* out_bits) {
+    __shared__ double red[33];
+    const int c = blockIdx.x;
+    const double th = theta[c];
+    double s = 0.0;
+    for (int64_t r = threadIdx.x; r < n; r += 256) {
+        const double d = Z[(int64_t)c * n + r] - th * QW[(int64_t)c * n + r];
+        s = fma(d, d, s);
+    }
+    s = block_sum<256>(s, red);
+    if (threadIdx.x == 0) {
+        double rel = sqrt(s) / fabs(theta[0]);
+        if (!isfinite(rel)) rel = INFINITY;
+        atomicMax(out_bits, (unsigned long long)__double_as_longlong(rel));
+    }
+}
+
+// U[r*dn + i] = QW[i*n + r]
+__global__ void k_to_isometry(const double* QW, int64_t n, int dn, double* U) {
+    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= n * dn) return;
+    const int64_t r = e / dn, i = e % dn;
+    U[e] = QW[i * n + r];
+}
+
+}  // namespace
+
+static void set_smem(const void* fn, size_t bytes) {
+    TRG_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+}
+
+// Column-major n x m "A^T B" (m x m result, row-major) and "A W" products.
+static void gram(Ctx& ctx, const double* A, const double* B, int64_t n, int m, double* G, int precision) {
+    GemmDesc g;
+    g.M = m; g.N = m; g.K = n;
+    g.A.base = A; g.A.off_r = ctx.table({{m, n}}); g.A.off_c = ctx.table({{n, 1}}); g.A.c_fast = true;
+    g.B.base = B; g.B.off_r = ctx.table({{n, 1}}); g.B.off_c = ctx.table({{m, n}}); g.B.c_fast = false;
+    g.C = G; g.c_m = ctx.table({{m, m}}); g.c_n = ctx.table({{m, 1}}); g.beta = 0.0;
+    gemm(ctx, g, precision);
+}
+static void times_small(Ctx& ctx, const double* A, const double* W, int64_t n, int m, double* C) {
+    GemmDesc g;
+    g.M = n; g.N = m; g.K = m;
+    g.A.base = A; g.A.off_r = ctx.table({{n, 1}}); g.A.off_c = ctx.table({{m, n}}); g.A.c_fast = false;
+    g.B.base = W; g.B.off_r = ctx.table({{m, 1}}); g.B.off_c = ctx.table({{m, m}}); g.B.c_fast = false;
+    g.C = C; g.c_m = ctx.table({{n, 1}}); g.c_n = ctx.table({{m, n}}); g.beta = 0.0;
+    gemm(ctx, g, TRG_FP64);
+}
+
+// Orthonormalise the columns of Y in place (two Cholesky-QR passes).
+static void orthonormalise(Ctx& ctx, double* Y, int64_t n, int m, double* G, double* L, int* flags,
+                           int* nbad, uint64_t seed, uint64_t& salt) {
+    const size_t smem = (size_t)m * m * sizeof(double);
+    for (int pass = 0; pass < 2; ++pass) {
+        int attempt = 0;
+        for (;; ++attempt) {
+            TRG_CUDA(cudaMemsetAsync(flags, 0, (size_t)(m + 1) * sizeof(int), ctx.stream));
+            k_col_normalize<<<m, 256, 0, ctx.stream>>>(Y, n, flags);
+            TRG_LAUNCHED(ctx);
+            gram(ctx, Y, Y, n, m, G, TRG_FP64);
+            k_chol_flag<<<1, 256, smem, ctx.stream>>>(G, L, m, pass == 0 ? 1e-8 : 1e-12, flags, nbad);
+            TRG_LAUNCHED(ctx);
+            int hb = 0;
+            TRG_CUDA(cudaMemcpyAsync(&hb, nbad, sizeof(int), cudaMemcpyDeviceToHost, ctx.stream));
+            TRG_CUDA(cudaStreamSynchronize(ctx.stream));
+            if (hb == 0) break;
+            if (attempt >= 16) fail(TRG_ENUMERIC, "Cholesky-QR: could not complete a basis");
+            dim3 grid((unsigned)std::min<int64_t>((n + 255) / 256, 64), (unsigned)m);
+            k_rand_cols<<<grid, 256, 0, ctx.stream>>>(Y, n, m, flags, seed, ++salt);
+            TRG_LAUNCHED(ctx);
+        }
+        k_trsm_rows<<<(unsigned)((n + 127) / 128), 128, smem, ctx.stream>>>(Y, L, n, m);
+        TRG_LAUNCHED(ctx);
+    }
+}
+
+int isometry(Ctx& ctx, const double* M, int64_t n, int dcut, double* U, std::vector<double>& lam,
+             int step, int precision) {
+    const int dn_paper = (int)std::min<int64_t>(n, dcut);
+    const int m = (int)std::min<int64_t>(n, (int64_t)dn_paper + std::max(1, ctx.cfg.oversample));
+    if (m > MAX_M) fail(TRG_ENOTSUP, "isometry: Dcut + oversampling exceeds the supported block (112)");
+    static bool attrs = false;
+    if (!attrs) {
+        set_smem((const void*)k_chol_flag, (size_t)MAX_M * MAX_M * 8);
+        set_smem((const void*)k_trsm_rows, (size_t)MAX_M * MAX_M * 8);
+        set_smem((const void*)k_jacobi, (size_t)MAX_M * MAX_M * 8 + (MAX_M + 2) * 8 + (MAX_M + 2) * 4);
+        attrs = true;
+    }
+    // buffers: Q, Y, Z, QW (n x m each); G, L, W (m x m); theta (m)
+    ctx.ensure(ctx.eig, (size_t)(4 * n * m) * sizeof(double));
+    ctx.ensure(ctx.eig_small, (size_t)(3 * m * m + 2 * m + 8) * sizeof(double));
+    ctx.ensure(ctx.flags, (size_t)(m + 2) * sizeof(int));
+    double* Q = ctx.eig.as<double>();
+    double* Y = Q + n * m;
+    double* Z = Y + n * m;
+    double* QW = Z + n * m;
+    double* G = ctx.eig_small.as<double>();
+    double* L = G + m * m;
+    double* W = L + m * m;
+    double* theta = W + m * m;
+    int* flags = ctx.flags.as<int>();
+    int* nbad = flags + m;
+    int* status = ctx.status.as<int>();
+    double* res_slot = ctx.scal.as<double>() + SC_RES;
+    const uint64_t seed = ctx.cfg.seed ^ (0xA24BAED4963EE407ull * (uint64_t)step);
+    uint64_t salt = 0;
+
+    {
+        dim3 grid((unsigned)std::min<int64_t>((n + 255) / 256, 64), (unsigned)m);
+        k_rand_cols<<<grid, 256, 0, ctx.stream>>>(Q, n, m, nullptr, seed, salt);
+        TRG_LAUNCHED(ctx);
+    }
+    orthonormalise(ctx, Q, n, m, G, L, flags, nbad, seed, salt);
+
+    const size_t jac_smem = (size_t)m * m * 8 + (m + 2) * 8 + (m + 2) * 4;
+    std::vector<double> th((size_t)m);
+    const int max_it = std::max(1, ctx.cfg.eig_max_iter);
+    for (int it = 1; it <= max_it; ++it) {
+        // Y = M Q
+        GemmDesc g;
+        g.M = n; g.N = m; g.K = n;
+        g.A.base = M; g.A.off_r = ctx.table({{n, n}}); g.A.off_c = ctx.table({{n, 1}}); g.A.c_fast = true;
+        g.B.base = Q; g.B.off_r = ctx.table({{n, 1}}); g.B.off_c = ctx.table({{m, n}}); g.B.c_fast = false;
+        g.C = Y; g.c_m = ctx.table({{n, 1}}); g.c_n = ctx.table({{m, n}}); g.beta = 0.0;
+        gemm(ctx, g, precision);
+        // Rayleigh-Ritz
+        gram(ctx, Q, Y, n, m, G, TRG_FP64);
+        k_jacobi<<<1, 512, jac_smem, ctx.stream>>>(G, m, 1e-15, 60, theta, W, status);
+        TRG_LAUNCHED(ctx);
+        times_small(ctx, Y, W, n, m, Z);
+        times_small(ctx, Q, W, n, m, QW);
+        TRG_CUDA(cudaMemsetAsync(res_slot, 0, sizeof(double), ctx.stream));
+        k_residual<<<dn_paper, 256, 0, ctx.stream>>>(Z, QW, theta, n, (unsigned long long*)res_slot);
+        TRG_LAUNCHED(ctx);
+        double res = 0.0;
+        TRG_CUDA(cudaMemcpyAsync(th.data(), theta, (size_t)m * sizeof(double), cudaMemcpyDeviceToHost, ctx.stream));
+        TRG_CUDA(cudaMemcpyAsync(&res, res_slot, sizeof(double), cudaMemcpyDeviceToHost, ctx.stream));
+        TRG_CUDA(cudaStreamSynchronize(ctx.stream));
+        if (read_status(ctx) & ST_EIG_NOCONV) fail(TRG_ENUMERIC, "Rayleigh-Ritz Jacobi did not converge");
+        if (!(th[0] > 0.0) || !std::isfinite(th[0])) fail(TRG_ENUMERIC, "environment has no positive eigenvalue");
+        if (res <= ctx.cfg.eig_tol || m == n) {
+            int dn = dn_paper;
+            if (ctx.cfg.trunc == TRG_TRUNC_MULTIPLET && dn < n) {
+                while (dn > 1 && (th[(size_t)dn - 1] - th[(size_t)dn]) < ctx.cfg.gap_tol * th[0]) --dn;
+            }
+            lam.assign(th.begin(), th.begin() + dn);
+            const int64_t tot = n * dn;
+            k_to_isometry<<<(unsigned)((tot + 255) / 256), 256, 0, ctx.stream>>>(QW, n, dn, U);
+            TRG_LAUNCHED(ctx);
+            return dn;
+        }
+        // next block: orth(Y W) = orth(M Q W), same span as M Q
+        std::swap(Q, Z);
+        orthonormalise(ctx, Q, n, m, G, L, flags, nbad, seed, salt);
+    }
+    fail(TRG_ENUMERIC, "subspace iteration did not converge");
+}
+
+}  // namespace trg

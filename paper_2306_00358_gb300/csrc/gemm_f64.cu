@@ -1,0 +1,103 @@
+// Plain FP64 gathered GEMM on the CUDA cores (the TRG_FP64 precision mode).
+//
+// Every contraction of the HOTRG step (environment, U.T.T.U, M.Q products of
+// the subspace iteration) is a matrix product once its multi-indices are
+// flattened; offset tables do the flattening, so permuted and rotated views
+// (the y half-step) cost nothing extra.  64x64 output tile per 256-thread
+// block, K in steps of 16 through shared memory, 4x4 outputs per thread.
+#include "internal.h"
+
+namespace trg {
+
+namespace {
+
+constexpr int BM = 64, BN = 64, BK = 16, NT = 256;
+
+struct GemmArgs {
+    int64_t M, N, K;
+    const double* A; const int64_t* a_m; const int64_t* a_k; int a_kfast;
+    const double* B; const int64_t* b_k; const int64_t* b_n; int b_nfast;
+    double* C; const int64_t* c_m; const int64_t* c_n;
+    double beta;
+};
+
+__global__ void __launch_bounds__(NT) k_gemm_f64(const GemmArgs g) {
+    __shared__ double As[BK][BM + 1];
+    __shared__ double Bs[BK][BN + 1];
+    const int tid = threadIdx.x;
+    const int tx = tid % 16, ty = tid / 16;
+    const int64_t m0 = (int64_t)blockIdx.y * BM;
+    const int64_t n0 = (int64_t)blockIdx.x * BN;
+
+    double acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+
+    for (int64_t k0 = 0; k0 < g.K; k0 += BK) {
+#pragma unroll
+        for (int e = tid; e < BM * BK; e += NT) {
+            int r, kk;
+            if (g.a_kfast) { kk = e % BK; r = e / BK; } else { r = e % BM; kk = e / BM; }
+            const int64_t m = m0 + r, k = k0 + kk;
+            double v = 0.0;
+            if (m < g.M && k < g.K) v = g.A[g.a_m[m] + g.a_k[k]];
+            As[kk][r] = v;
+        }
+#pragma unroll
+        for (int e = tid; e < BN * BK; e += NT) {
+            int c, kk;
+            if (g.b_nfast) { c = e % BN; kk = e / BN; } else { kk = e % BK; c = e / BK; }
+            const int64_t n = n0 + c, k = k0 + kk;
+            double v = 0.0;
+            if (n < g.N && k < g.K) v = g.B[g.b_k[k] + g.b_n[n]];
+            Bs[kk][c] = v;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < BK; ++kk) {
+            double a[4], b[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx + 16 * j];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int64_t m = m0 + ty + 16 * i;
+        if (m >= g.M) continue;
+        const int64_t cm = g.c_m[m];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int64_t n = n0 + tx + 16 * j;
+            if (n >= g.N) continue;
+            double* dst = g.C + cm + g.c_n[n];
+            *dst = (g.beta != 0.0) ? fma(g.beta, *dst, acc[i][j]) : acc[i][j];
+        }
+    }
+}
+
+}  // namespace
+
+void gemm_f64(Ctx& ctx, const GemmDesc& d) {
+    if (d.M <= 0 || d.N <= 0) return;
+    GemmArgs g;
+    g.M = d.M; g.N = d.N; g.K = d.K;
+    g.A = d.A.base; g.a_m = d.A.off_r; g.a_k = d.A.off_c; g.a_kfast = d.A.c_fast ? 1 : 0;
+    g.B = d.B.base; g.b_k = d.B.off_r; g.b_n = d.B.off_c; g.b_nfast = d.B.c_fast ? 1 : 0;
+    g.C = d.C; g.c_m = d.c_m; g.c_n = d.c_n; g.beta = d.beta;
+    const int64_t gx = (d.N + BN - 1) / BN, gy = (d.M + BM - 1) / BM;
+    if (gy > 65535) fail(TRG_EINVAL, "gemm_f64: too many row tiles");
+    dim3 grid((unsigned)gx, (unsigned)gy);
+    k_gemm_f64<<<grid, NT, 0, ctx.stream>>>(g);
+    TRG_LAUNCHED(ctx);
+}
+
+}  // namespace trg

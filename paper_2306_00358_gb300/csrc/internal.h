@@ -1,0 +1,159 @@
+// Internal declarations of libtrg (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "trg.h"
+
+namespace trg {
+
+// ------------------------------------------------------------ errors ----
+struct Error {
+    int status;
+    std::string msg;
+};
+
+[[noreturn]] void fail(int status, const std::string& msg);
+void check_cuda(cudaError_t e, const char* what, const char* file, int line);
+#define TRG_CUDA(call) ::trg::check_cuda((call), #call, __FILE__, __LINE__)
+// After every launch: catch configuration errors immediately.
+#define TRG_LAUNCHED(ctx) do { (ctx).launches++; ::trg::check_cuda(cudaGetLastError(), "kernel launch", __FILE__, __LINE__); } while (0)
+
+// Device status word bits (written by kernels, read by the host at sync points).
+enum : int {
+    ST_BAD_NORM = 1,       // norm <= 0, NaN or inf
+    ST_BAD_TRACE = 2,      // trace <= 0 or NaN
+    ST_EIG_NOCONV = 4,     // Jacobi sweeps exhausted
+    ST_CHOL_BREAK = 8,     // Cholesky pivot could not be repaired
+    ST_TIMEOUT = 16,       // a bounded device wait ran out
+    ST_BOUNDS = 32         // a checked index fell outside its buffer (skipped)
+};
+
+// ------------------------------------------------------- device memory ----
+struct Buf {
+    void* p = nullptr;
+    size_t bytes = 0;
+    template <class T> T* as() const { return static_cast<T*>(p); }
+};
+
+// A rank-4 strided view of FP64 device memory (element strides).
+struct View4 {
+    double* p;
+    int64_t n[4];
+    int64_t s[4];
+};
+
+struct Ctx {
+    int device = 0;
+    int sm_count = 0;
+    cudaStream_t stream = nullptr;
+    trg_config cfg{};
+    trg_alloc_fn alloc_fn = nullptr;
+    trg_free_fn free_fn = nullptr;
+    void* alloc_user = nullptr;
+    std::string last_error;
+    uint64_t launches = 0;
+
+    // ---- solve state
+    bool have_tensor = false;
+    int Dx = 0, Dy = 0;
+    int steps = 0;
+    double beta = 0.0;
+    Buf T, Tnext;          // current / next site tensor
+    Buf M;                 // environment
+    Buf U;                 // isometry (n x Dn row-major)
+    Buf scal;              // device scalars, see SC_* below
+    Buf status;            // device status word (int)
+    std::vector<std::vector<double>> spectra;
+
+    // ---- scratch
+    Buf ws;                // contraction workspace (X1, X2 slices)
+    Buf envP, envQ;        // environment intermediates
+    Buf eig;               // subspace-iteration buffers
+    Buf eig_small;         // m x m buffers
+    Buf flags;             // per-column flags (int)
+    std::map<std::string, Buf> tables;  // cached offset tables
+
+    // ---- phase timing
+    bool prof = false;
+    int phase = TRG_PHASE_ENV;
+    struct PhaseAcc {
+        double ms = 0.0, flops = 0.0, mma_flops = 0.0;
+        uint64_t calls = 0;
+        std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pending;
+    } ph[TRG_PHASE_COUNT];
+    std::vector<cudaEvent_t> event_pool;
+    cudaEvent_t get_event();
+    // Record the start of a timed region of phase p (no-op unless profiling).
+    int region_begin(int p);
+    void region_end(int token, double flops, double mma_flops);
+    void collect_timings();
+
+    void* raw_alloc(size_t bytes);
+    void raw_free(void* p, size_t bytes);
+    void ensure(Buf& b, size_t bytes);
+    void release(Buf& b);
+    const int64_t* table(const std::vector<std::pair<int64_t, int64_t>>& modes);
+};
+
+// Device scalar slots (doubles) in Ctx::scal.
+enum : int {
+    SC_LOGNORM = 0,   // sum_k 2^-k ln n_k
+    SC_LN_N0 = 1,     // ln n0
+    SC_NORM = 2,      // last max|T| (as the bits of a non-negative double)
+    SC_TRACE = 3,     // last trace
+    SC_RES = 4,       // max Ritz residual / lambda_1 (subspace iteration)
+    SC_COUNT = 8
+};
+
+// ------------------------------------------------------------ GEMM ----
+// C[c_m[m] + c_n[n]] = sum_k A[a_m[m] + a_k[k]] * B[b_k[k] + b_n[n]]  (+ beta*C)
+// Offset tables (int64, elements) make any strided multi-index layout a
+// plain matrix for the kernels.
+struct Gather {
+    const double* base;
+    const int64_t* off_r;   // row offsets   (A: m, B: k, C: m)
+    const int64_t* off_c;   // col offsets   (A: k, B: n, C: n)
+    bool c_fast;            // consecutive columns are adjacent in memory
+};
+struct GemmDesc {
+    int64_t M, N, K;
+    Gather A, B;
+    double* C;
+    const int64_t* c_m;
+    const int64_t* c_n;
+    double beta;            // 0: overwrite, 1: accumulate
+};
+void gemm(Ctx& ctx, const GemmDesc& g, int precision);
+void gemm_f64(Ctx& ctx, const GemmDesc& g);
+
+// Table helpers: enumerate all index tuples of `modes` (size, stride),
+// first mode slowest, and return the device table of offsets.
+std::vector<int64_t> build_table(const std::vector<std::pair<int64_t, int64_t>>& modes);
+
+// ------------------------------------------------------ path pieces ----
+int precision_for_step(const Ctx& ctx, int step);
+void environment(Ctx& ctx, const View4& t, double* M, int precision);
+void contract(Ctx& ctx, const View4& t, const double* U, int64_t Dn, const View4& out, int precision);
+// Returns Dn actually kept; lam (host) gets the kept eigenvalues.
+int isometry(Ctx& ctx, const double* M, int64_t n, int dcut, double* U, std::vector<double>& lam,
+             int step, int precision);
+
+// Small kernels (small_kernels.cu)
+void launch_init_ising(Ctx& ctx, double* T, double beta, double h);
+void launch_init_xy(Ctx& ctx, double* T, int d0, double beta, double h);
+void launch_maxabs(Ctx& ctx, const double* x, int64_t n, double* slot_bits);
+void launch_normalise(Ctx& ctx, double* x, int64_t n, int step_weight_exp, bool initial);
+void launch_trace(Ctx& ctx, const double* T, int64_t Dx, int64_t Dy, double* slot);
+void launch_identity(Ctx& ctx, double* U, int64_t n);
+void launch_fill(Ctx& ctx, double* x, int64_t n, double v);
+void launch_copy_strided(Ctx& ctx, const View4& src, const View4& dst);
+
+int read_status(Ctx& ctx);  // synchronises the stream
+
+}  // namespace trg

@@ -1,0 +1,180 @@
+// The HOTRG half-step as flattened matrix products (Sec. 2, coarse-graining
+// listing): environment M, U.T.T.U contraction, plus the offset tables that
+// turn the index wiring (and the y-direction rotation) into plain GEMMs.
+#include <algorithm>
+#include <cstring>
+#include <sstream>
+
+#include "internal.h"
+
+namespace trg {
+
+std::vector<int64_t> build_table(const std::vector<std::pair<int64_t, int64_t>>& modes) {
+    int64_t total = 1;
+    for (auto& m : modes) total *= m.first;
+    std::vector<int64_t> out((size_t)std::max<int64_t>(total, 0));
+    if (total <= 0) return out;
+    std::vector<int64_t> idx(modes.size(), 0);
+    for (int64_t e = 0; e < total; ++e) {
+        int64_t off = 0;
+        for (size_t q = 0; q < modes.size(); ++q) off += idx[q] * modes[q].second;
+        out[(size_t)e] = off;
+        for (int q = (int)modes.size() - 1; q >= 0; --q) {
+            if (++idx[(size_t)q] < modes[(size_t)q].first) break;
+            idx[(size_t)q] = 0;
+        }
+    }
+    return out;
+}
+
+const int64_t* Ctx::table(const std::vector<std::pair<int64_t, int64_t>>& modes) {
+    std::ostringstream key;
+    for (auto& m : modes) key << m.first << ':' << m.second << ';';
+    auto it = tables.find(key.str());
+    if (it != tables.end()) return it->second.as<int64_t>();
+    std::vector<int64_t> h = build_table(modes);
+    Buf b;
+    ensure(b, std::max<size_t>(8, h.size() * sizeof(int64_t)));
+    if (!h.empty())
+        TRG_CUDA(cudaMemcpyAsync(b.p, h.data(), h.size() * sizeof(int64_t), cudaMemcpyHostToDevice, stream));
+    // the host vector dies here: wait for the copy (tables are built once per shape)
+    TRG_CUDA(cudaStreamSynchronize(stream));
+    tables[key.str()] = b;
+    return b.as<int64_t>();
+}
+
+using Modes = std::vector<std::pair<int64_t, int64_t>>;
+
+static bool unit_first_stride(const Modes& m) {
+    // consecutive flat indices are adjacent iff the fastest mode has stride 1
+    return !m.empty() && m.back().second == 1 && m.back().first > 1;
+}
+
+static Gather gather(Ctx& ctx, const double* base, const Modes& rows, const Modes& cols) {
+    Gather g;
+    g.base = base;
+    g.off_r = ctx.table(rows);
+    g.off_c = ctx.table(cols);
+    g.c_fast = unit_first_stride(cols);
+    return g;
+}
+
+void gemm_split(Ctx& ctx, const GemmDesc& g);  // split_gemm.cu
+
+void gemm(Ctx& ctx, const GemmDesc& g, int precision) {
+    // products inside the isometry are timed as part of that phase
+    const int tok = (ctx.phase == TRG_PHASE_EIG) ? -1 : ctx.region_begin(ctx.phase);
+    if (precision == TRG_FP64) gemm_f64(ctx, g);
+    else if (precision == TRG_SPLIT_BF16) gemm_split(ctx, g);
+    else fail(TRG_EINVAL, "unknown precision mode");
+    ctx.region_end(tok, 2.0 * (double)g.M * (double)g.N * (double)g.K, 0.0);
+}
+
+int precision_for_step(const Ctx& ctx, int step) {
+    if (ctx.cfg.precision == TRG_FP64) return TRG_FP64;
+    return (step - 1 < ctx.cfg.split_from_step) ? TRG_FP64 : ctx.cfg.precision;
+}
+
+// M[(i,j),(k,l)] = sum_{e,f} Q[i,e,k,f] P[j,e,l,f],
+// P[j,e,l,f] = sum_{a,b} t[j,a,b,e] t[l,a,b,f]   (upper pair, bond e / f)
+// Q[i,e,k,f] = sum_{c,d} t[i,e,c,d] t[k,f,c,d]   (lower pair)
+void environment(Ctx& ctx, const View4& t, double* M, int precision) {
+    const int64_t Dx = t.n[0], Dy = t.n[1];
+    const int64_t* s = t.s;
+    const int64_t DD = Dx * Dy;
+    ctx.ensure(ctx.envP, (size_t)(DD * DD) * sizeof(double));
+    ctx.ensure(ctx.envQ, (size_t)(DD * DD) * sizeof(double));
+    double* P = ctx.envP.as<double>();
+    double* Q = ctx.envQ.as<double>();
+
+    {   // P: rows (j,e), k (a,b), cols (l,f)
+        const Modes r = {{Dx, s[0]}, {Dy, s[3]}}, k = {{Dy, s[1]}, {Dx, s[2]}};
+        GemmDesc g;
+        g.M = DD; g.N = DD; g.K = DD;
+        g.A = gather(ctx, t.p, r, k);
+        g.B = gather(ctx, t.p, k, r);
+        g.C = P; g.c_m = ctx.table({{DD, DD}}); g.c_n = ctx.table({{DD, 1}});
+        g.beta = 0.0;
+        gemm(ctx, g, precision);
+    }
+    {   // Q: rows (i,e), k (c,d), cols (k,f)
+        const Modes r = {{Dx, s[0]}, {Dy, s[1]}}, k = {{Dx, s[2]}, {Dy, s[3]}};
+        GemmDesc g;
+        g.M = DD; g.N = DD; g.K = DD;
+        g.A = gather(ctx, t.p, r, k);
+        g.B = gather(ctx, t.p, k, r);
+        g.C = Q; g.c_m = ctx.table({{DD, DD}}); g.c_n = ctx.table({{DD, 1}});
+        g.beta = 0.0;
+        gemm(ctx, g, precision);
+    }
+    {   // M: rows (i,k), k (e,f), cols (j,l); stored M[(i,j),(k,l)]
+        GemmDesc g;
+        g.M = Dx * Dx; g.N = Dx * Dx; g.K = Dy * Dy;
+        g.A = gather(ctx, Q, {{Dx, Dy * DD}, {Dx, Dy}}, {{Dy, DD}, {Dy, 1}});
+        g.B = gather(ctx, P, {{Dy, DD}, {Dy, 1}}, {{Dx, Dy * DD}, {Dx, Dy}});
+        g.C = M;
+        g.c_m = ctx.table({{Dx, Dx * Dx * Dx}, {Dx, Dx}});
+        g.c_n = ctx.table({{Dx, Dx * Dx}, {Dx, 1}});
+        g.beta = 0.0;
+        gemm(ctx, g, precision);
+    }
+}
+
+// Tx[i,j,k,l] = sum U[a,b,i] t[b,j,d,c] t[a,c,e,l] U[e,d,k], in slices of j:
+//   X1[(jj,i,d),(a,c)] = sum_b U[a,b,i] t[b,j0+jj,d,c]          (D^6)
+//   X2[(jj,i,d),(e,l)] = sum_{a,c} X1[(jj,i,d),(a,c)] t[a,c,e,l]  (D^7)
+//   O[i,j0+jj,k,l]     = sum_{d,e} X2[(jj,i,d),(e,l)] U[e,d,k]    (D^6)
+void contract(Ctx& ctx, const View4& t, const double* U, int64_t Dn, const View4& out, int precision) {
+    const int64_t Dx = t.n[0], Dy = t.n[1];
+    const int64_t* s = t.s;
+    const int64_t* o = out.s;
+    const int64_t DD = Dx * Dy;
+    const size_t ws_cap = ctx.cfg.workspace_bytes ? ctx.cfg.workspace_bytes : ((size_t)4 << 30);
+    const size_t per_j = (size_t)(2 * Dn * Dx * DD) * sizeof(double);
+    int64_t jb = std::max<int64_t>(1, std::min<int64_t>(Dy, (int64_t)(ws_cap / per_j)));
+    ctx.ensure(ctx.ws, per_j * (size_t)jb);
+    double* X1 = ctx.ws.as<double>();
+    double* X2 = X1 + jb * Dn * Dx * DD;
+
+    for (int64_t j0 = 0; j0 < Dy; j0 += jb) {
+        const int64_t jn = std::min(jb, Dy - j0);
+        {   // X1
+            ctx.phase = TRG_PHASE_X1;
+            GemmDesc g;
+            g.M = Dx * Dn; g.N = jn * DD; g.K = Dx;
+            g.A = gather(ctx, U, {{Dx, Dx * Dn}, {Dn, 1}}, {{Dx, Dn}});
+            g.B = gather(ctx, t.p + j0 * s[1], {{Dx, s[0]}}, {{jb, s[1]}, {Dx, s[2]}, {Dy, s[3]}});
+            g.C = X1;
+            g.c_m = ctx.table({{Dx, Dy}, {Dn, Dx * DD}});
+            g.c_n = ctx.table({{jb, Dn * Dx * DD}, {Dx, DD}, {Dy, 1}});
+            g.beta = 0.0;
+            gemm(ctx, g, precision);
+        }
+        {   // X2 (the D^7 product)
+            ctx.phase = TRG_PHASE_X2;
+            GemmDesc g;
+            g.M = jn * Dn * Dx; g.N = DD; g.K = DD;
+            g.A = gather(ctx, X1, {{jb * Dn * Dx, DD}}, {{DD, 1}});
+            g.B = gather(ctx, t.p, {{Dx, s[0]}, {Dy, s[1]}}, {{Dx, s[2]}, {Dy, s[3]}});
+            g.C = X2;
+            g.c_m = ctx.table({{jb * Dn * Dx, DD}});
+            g.c_n = ctx.table({{DD, 1}});
+            g.beta = 0.0;
+            gemm(ctx, g, precision);
+        }
+        {   // O
+            ctx.phase = TRG_PHASE_X3;
+            GemmDesc g;
+            g.M = jn * Dn * Dy; g.N = Dn; g.K = Dx * Dx;
+            g.A = gather(ctx, X2, {{jb, Dn * Dx * DD}, {Dn, Dx * DD}, {Dy, 1}}, {{Dx, DD}, {Dx, Dy}});
+            g.B = gather(ctx, U, {{Dx, Dn}, {Dx, Dx * Dn}}, {{Dn, 1}});
+            g.C = out.p + j0 * o[1];
+            g.c_m = ctx.table({{jb, o[1]}, {Dn, o[0]}, {Dy, o[3]}});
+            g.c_n = ctx.table({{Dn, o[2]}});
+            g.beta = 0.0;
+            gemm(ctx, g, precision);
+        }
+    }
+}
+
+}  // namespace trg

@@ -1,0 +1,75 @@
+"""Write the oracle's expected values for the GPU parity tests.
+
+Calls only the oracle (oracle/), never the CUDA library.  Run from the
+repository root:  python tests/golden/make_golden.py
+"""
+from __future__ import annotations
+
+import json
+import math
+import os
+import sys
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, os.path.dirname(os.path.dirname(HERE)))
+
+from oracle import exact, hotrg, models  # noqa: E402
+
+CASES = [
+    # name, model, beta, h, dcut, nsteps, trunc
+    ("ising_b0.44_d16_n40", "ising", 0.44, 0.0, 16, 40, "paper"),
+    ("ising_bc_d16_h1e-3_n40", "ising", exact.BETA_C, 1e-3, 16, 40, "paper"),
+    ("ising_b0.48_d10_n21", "ising", 0.48, 0.0, 10, 21, "paper"),
+    ("xy_b1.0_d12_n12", "xy", 1.0, 0.0, 12, 12, "multiplet"),
+    ("xy_b1.1_d20_h0.05_n8", "xy", 1.1, 0.05, 20, 8, "multiplet"),
+]
+
+
+def run(name, model, beta, h, dcut, nsteps, trunc):
+    t0 = models.initial_tensor(model, beta, h)
+    s = hotrg.solve(t0, beta, dcut, nsteps, trunc=trunc, keep_full_spectra=True)
+    steps = []
+    for k, (kept, full) in enumerate(zip(s.spectra, s.full_spectra), start=1):
+        n = full.shape[0]
+        dn = kept.shape[0]
+        truncated = dn < n
+        gap = float((full[dn - 1] - full[dn]) / full[0]) if truncated else None
+        steps.append({"step": k, "n": int(n), "dn": int(dn), "truncated": bool(truncated),
+                      "kept": [float(x) for x in kept] if truncated else [], "gap": gap,
+                      "dims": list(s.dims[k - 1])})
+    rec = {"name": name, "model": model, "beta": beta, "h": h, "dcut": dcut, "nsteps": nsteps,
+           "trunc": trunc, "f": s.f, "lnz_per_site": s.lnz_per_site, "steps": steps,
+           "source": "oracle/hotrg.py solve() (CPU FP64, cyclic Jacobi)"}
+    if model == "ising" and h == 0.0:
+        rec["f_onsager"] = exact.onsager_free_energy(beta)
+    return rec
+
+
+def main():
+    out = {}
+    for case in CASES:
+        print("oracle:", case[0], flush=True)
+        out[case[0]] = run(*case)
+    with open(os.path.join(HERE, "oracle_solves.json"), "w") as fh:
+        json.dump(out, fh, indent=1)
+    # exact partition functions of small tori (no truncation)
+    ex = {}
+    for (beta, h) in [(0.44, 0.0), (0.44, 0.01), (0.3, -0.25)]:
+        for nsteps in (2, 3, 4):
+            w, hh = exact.hotrg_block(nsteps)
+            ex[f"ising_b{beta}_h{h}_n{nsteps}"] = {"model": "ising", "beta": beta, "h": h, "nsteps": nsteps,
+                                                   "width": w, "height": hh,
+                                                   "lnz": exact.ising_lnz_exact(w, hh, beta, h)}
+    for (beta, h) in [(1.0, 0.0), (0.9, 0.1)]:
+        for nsteps in (1, 2):
+            w, hh = exact.hotrg_block(nsteps)
+            ex[f"xy_b{beta}_h{h}_n{nsteps}"] = {"model": "xy", "beta": beta, "h": h, "nsteps": nsteps,
+                                                "width": w, "height": hh,
+                                                "lnz": exact.xy_lnz_exact(w, hh, beta, h, 9)}
+    with open(os.path.join(HERE, "exact_tori.json"), "w") as fh:
+        json.dump(ex, fh, indent=1)
+    print("wrote oracle_solves.json, exact_tori.json")
+
+
+if __name__ == "__main__":
+    main()

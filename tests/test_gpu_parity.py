@@ -1,0 +1,188 @@
+"""GPU path vs the CPU oracle, element by element where the result is unique.
+
+Components are compared on seeded random inputs (environment and contraction
+element-wise; isometry through its eigenvalues and its projector), full solves
+through the free energy and the kept spectrum of every truncated half-step
+(tensors are not compared: they carry a gauge freedom).
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+from oracle import exact, hotrg, jacobi, models
+from paper_2306_00358_gb300 import Solver, TRGError, workloads
+
+pytestmark = pytest.mark.gpu
+HERE = os.path.dirname(os.path.abspath(__file__))
+GOLDEN = json.load(open(os.path.join(HERE, "golden", "oracle_solves.json")))
+TORI = json.load(open(os.path.join(HERE, "golden", "exact_tori.json")))
+
+F_TOL_FP64 = 1e-10          # |f_gpu - f_oracle|, FP64 path
+SPEC_TOL = 1e-9             # |lam_gpu - lam_oracle| / lam_1
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    return torch
+
+
+def _solver(**kw):
+    return Solver(0, **kw)
+
+
+# ------------------------------------------------------------ components ---
+@pytest.mark.parametrize("dx,dy", [(2, 2), (5, 3), (8, 8), (12, 7), (17, 9)])
+def test_environment_matches_oracle(torch, dx, dy):
+    t = workloads.random_tensor((dx, dy, dx, dy), seed=100 + dx * dy)
+    ref = hotrg.environment_x(t)
+    with _solver() as s:
+        m = s.environment(torch.from_numpy(t).cuda()).cpu().numpy()
+    assert m.shape == ref.shape
+    assert np.abs(m - ref).max() <= 1e-13 * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("dx,dy,dn,ws", [(2, 2, 4, 0), (5, 3, 7, 0), (8, 8, 20, 0), (12, 7, 33, 0),
+                                         (9, 10, 17, 200_000), (16, 16, 64, 3_000_000)])
+def test_contraction_matches_oracle(torch, dx, dy, dn, ws):
+    # ws > 0 forces several j-slices (and a ragged last slice)
+    t = workloads.random_tensor((dx, dy, dx, dy), seed=200 + dx + dy)
+    u = workloads.random_isometry(dx, dn, seed=300 + dn)
+    ref = hotrg.contract_x(t, u)
+    with _solver(workspace_bytes=ws) as s:
+        out = s.contract(torch.from_numpy(t).cuda(), torch.from_numpy(u).cuda()).cpu().numpy()
+    assert out.shape == (dn, dy, dn, dy)
+    assert np.abs(out - ref).max() <= 1e-13 * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("n,dcut,decades", [(36, 8, 12), (100, 20, 14), (144, 40, 20), (400, 48, 30)])
+def test_isometry_matches_oracle(torch, n, dcut, decades):
+    m = workloads.graded_psd(n, decades, seed=n)
+    lam_ref, v_ref, _ = jacobi.eigh(m)
+    with _solver() as s:
+        u, lam, dn = s.isometry(torch.from_numpy(m).cuda(), dcut)
+        u = u.cpu().numpy()
+    assert dn == dcut
+    assert np.abs(lam - lam_ref[:dn]).max() <= SPEC_TOL * lam_ref[0]
+    assert np.abs(u.T @ u - np.eye(dn)).max() <= 1e-12
+    # the kept subspace: compare projectors on the well-separated part
+    p_gpu = u @ u.T
+    p_ref = v_ref[:, :dn] @ v_ref[:, :dn].T
+    assert np.abs(p_gpu - p_ref).max() <= 1e-6
+
+
+def test_isometry_untruncated_is_identity(torch):
+    m = workloads.graded_psd(16, 5, seed=1)
+    with _solver() as s:
+        u, lam, dn = s.isometry(torch.from_numpy(m).cuda(), 16)
+    assert dn == 16 and lam is None
+    assert np.array_equal(u.cpu().numpy(), np.eye(16))
+
+
+# ----------------------------------------------------------- full solves ---
+@pytest.mark.parametrize("name", sorted(GOLDEN))
+def test_solve_matches_oracle(torch, name):
+    g = GOLDEN[name]
+    with _solver(trunc=g["trunc"]) as s:
+        s.init_tensor(g["model"], g["beta"], g["h"])
+        s.coarse_grain(g["dcut"], g["nsteps"])
+        f, lnz = s.free_energy()
+        spectra = [s.spectrum(k) for k in range(1, g["nsteps"] + 1)]
+        _, dx, dy, _ = s.state()
+    assert [dx, dy] == g["steps"][-1]["dims"]
+    assert abs(f - g["f"]) <= F_TOL_FP64, (f, g["f"])
+    for st, lam in zip(g["steps"], spectra):
+        if not st["truncated"]:
+            assert lam.size == 0
+            continue
+        ref = np.array(st["kept"])
+        assert lam.size == ref.size
+        assert np.abs(lam - ref).max() <= SPEC_TOL * ref[0], st["step"]
+
+
+@pytest.mark.parametrize("key", sorted(TORI))
+def test_untruncated_solve_matches_enumeration(torch, key):
+    e = TORI[key]
+    with _solver() as s:
+        s.init_tensor(e["model"], e["beta"], e["h"])
+        s.coarse_grain(10 ** 6, e["nsteps"])
+        _, lnz = s.free_energy()
+    v = e["width"] * e["height"]
+    assert abs(lnz * v - e["lnz"]) <= 1e-12 * max(1.0, abs(e["lnz"]))
+
+
+def test_onsager_dcut16(torch):
+    beta = 0.44
+    with _solver() as s:
+        s.init_tensor("ising", beta, 0.0)
+        s.coarse_grain(16, 40)
+        f, _ = s.free_energy()
+    fe = exact.onsager_free_energy(beta)
+    assert abs(f - fe) / abs(fe) <= 2e-6
+
+
+def test_resumable_and_odd_step_counts(torch):
+    # 40 half-steps in pieces equal 40 in one call; an odd count closes a 2^(n+1)/2 x 2^(n-1)/2 torus
+    with _solver() as a, _solver() as b:
+        a.init_tensor("ising", 0.44, 0.0)
+        a.coarse_grain(8, 40)
+        b.init_tensor("ising", 0.44, 0.0)
+        for chunk in (1, 2, 7, 30):
+            b.coarse_grain(8, chunk)
+        assert a.free_energy()[0] == b.free_energy()[0]
+    e = TORI["ising_b0.44_h0.01_n3"]
+    with _solver() as s:
+        s.init_tensor("ising", 0.44, 0.01)
+        s.coarse_grain(64, 3)
+        _, lnz = s.free_energy()
+    assert abs(lnz * 8 - e["lnz"]) <= 1e-12 * abs(e["lnz"])
+
+
+def test_zero_steps_is_single_site(torch):
+    beta, h = 0.37, 0.21
+    with _solver() as s:
+        s.init_tensor("ising", beta, h)
+        _, lnz = s.free_energy()
+    ref = math.log(sum(math.exp(2 * beta + beta * h * sp) for sp in (1, -1)))
+    assert abs(lnz - ref) <= 1e-14
+
+
+def test_raw_tensor_and_rotation(torch):
+    # a 4x4 torus of a random positive tensor and of its rotation
+    t = workloads.random_tensor((2, 3, 2, 3), seed=8, positive=True)
+    ref = hotrg.solve(t, 1.0, 10 ** 6, 4).lnz_per_site
+    with _solver() as s:
+        s.init_tensor_raw(t, 1.0)
+        s.coarse_grain(10 ** 6, 4)
+        _, a = s.free_energy()
+        s.init_tensor_raw(np.ascontiguousarray(t.transpose(1, 2, 3, 0)), 1.0)
+        s.coarse_grain(10 ** 6, 4)
+        _, b = s.free_energy()
+    assert abs(a - ref) <= 1e-13 and abs(b - ref) <= 1e-13
+
+
+# ----------------------------------------------------------- edge cases ---
+def test_errors_are_reported(torch):
+    with _solver() as s:
+        with pytest.raises(TRGError) as e:
+            s.coarse_grain(16, 1)
+        assert e.value.status == 2          # TRG_ESTATE
+        with pytest.raises(TRGError) as e:
+            s.init_tensor("ising", -1.0, 0.0)
+        assert e.value.status == 1          # TRG_EINVAL
+        with pytest.raises(TRGError) as e:
+            s.init_tensor("xy", 1.0, 0.0, d0=8)
+        assert e.value.status == 1
+        with pytest.raises(TRGError) as e:
+            s.init_tensor_raw(np.zeros((2, 2, 2, 2)), 1.0)
+        assert e.value.status == 4          # TRG_ENUMERIC: zero tensor
+        s.init_tensor("ising", 0.44, 0.0)
+        with pytest.raises(TRGError) as e:
+            s.coarse_grain(0, 1)
+        assert e.value.status == 1
+        s.coarse_grain(4, 2)                # the context is still usable
+        assert np.isfinite(s.free_energy()[0])
