@@ -173,7 +173,7 @@ def run_native(args):
     if world > 1:
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
-    precision = args.precision or "fp64"
+    precision = args.precision or "split"
     steps = args.steps or (2 if precision == "fp64" else 10)
     warmup = max(3, args.warmup)
 

@@ -65,12 +65,13 @@ typedef enum trg_trunc {
 
 typedef struct trg_config {
     int precision;           /* trg_precision (default TRG_FP64) */
-    int split_slices;        /* BF16 slices per operand in TRG_SPLIT_BF16, 2..6 (default 4) */
+    int split_slices;        /* BF16 slices per operand in TRG_SPLIT_BF16, 2..5 (default 4) */
     int split_from_step;     /* half-steps with index < this run in FP64 (default 0) */
     int trunc;               /* trg_trunc (default TRG_TRUNC_PAPER) */
     double gap_tol;          /* multiplet gap, relative to lambda_1 (default 1e-8) */
     int oversample;          /* subspace-iteration oversampling p (default 16) */
-    double eig_tol;          /* Ritz residual tolerance relative to lambda_1 (default 1e-12) */
+    double eig_tol;          /* Ritz residual tolerance relative to lambda_1 (default 1e-12; in
+                                TRG_SPLIT_BF16 at least 2^-(8*split_slices-10)) */
     int eig_max_iter;        /* subspace iterations before TRG_ENUMERIC (default 300) */
     uint64_t seed;           /* seed of the start block of the subspace iteration */
     size_t workspace_bytes;  /* bound on the contraction workspace (0 = 4 GiB) */
@@ -178,6 +179,16 @@ int trg_isometry(trg_ctx* ctx, const double* M_dev, int n, int Dcut,
  */
 int trg_contract(trg_ctx* ctx, const double* t_dev, const double* U_dev,
                  int Dx, int Dy, int Dn, double* Tx_dev);
+
+/*
+ * Plain matrix product C = A B in the context's precision mode (the kernel
+ * every contraction above is built on).  Row-major device matrices:
+ * A (M x K, leading dimension lda >= K), B (K x N, ldb >= N),
+ * C (M x N, ldc >= N); C is overwritten.  M, N, K >= 1; in TRG_SPLIT_BF16
+ * mode K <= 131072.
+ */
+int trg_gemm(trg_ctx* ctx, int M, int N, int K, const double* A_dev, int lda, const double* B_dev, int ldb,
+             double* C_dev, int ldc);
 
 /* ------------------------------------------------------- profiling ----- */
 /* Phases of a half-step, timed with CUDA events on the context's stream. */

@@ -244,7 +244,7 @@ int trg_config_default(trg_config* cfg) {
 
 static int validate_config(const trg_config& c) {
     if (c.precision != TRG_FP64 && c.precision != TRG_SPLIT_BF16) return TRG_EINVAL;
-    if (c.split_slices < 2 || c.split_slices > 6) return TRG_EINVAL;
+    if (c.split_slices < 2 || c.split_slices > 5) return TRG_EINVAL;
     if (c.split_from_step < 0) return TRG_EINVAL;
     if (c.trunc != TRG_TRUNC_PAPER && c.trunc != TRG_TRUNC_MULTIPLET) return TRG_EINVAL;
     if (!(c.gap_tol >= 0.0) || !(c.eig_tol > 0.0) || c.oversample < 1 || c.eig_max_iter < 1) return TRG_EINVAL;
@@ -293,7 +293,7 @@ int trg_destroy(trg_ctx* ctx) {
     cudaStreamSynchronize(ctx->stream);
     Ctx& c = *ctx;
     for (trg::Buf* b : {&c.T, &c.Tnext, &c.M, &c.U, &c.scal, &c.status, &c.ws, &c.envP, &c.envQ, &c.eig,
-                        &c.eig_small, &c.flags})
+                        &c.eig_small, &c.flags, &c.split_ws})
         c.release(*b);
     for (auto& kv : c.tables) c.release(kv.second);
     c.tables.clear();
@@ -491,6 +491,26 @@ int trg_contract(trg_ctx* ctx, const double* t_dev, const double* U_dev, int Dx,
     trg::View4 o = trg::contiguous_view(Tx_dev, Dn, Dy, Dn, Dy);
     trg::contract(*ctx, t, U_dev, Dn, o, ctx->cfg.precision);
     TRG_CUDA(cudaStreamSynchronize(ctx->stream));
+    return TRG_OK;
+    TRG_GUARD_END(ctx)
+}
+
+int trg_gemm(trg_ctx* ctx, int M, int N, int K, const double* A, int lda, const double* B, int ldb, double* C,
+             int ldc) {
+    if (!ctx) return TRG_EINVAL;
+    if (!A || !B || !C || M < 1 || N < 1 || K < 1 || lda < K || ldb < N || ldc < N)
+        return bad(ctx, TRG_EINVAL, "gemm: bad arguments");
+    TRG_GUARD_BEGIN
+    TRG_CUDA(cudaSetDevice(ctx->device));
+    trg::GemmDesc g;
+    g.M = M; g.N = N; g.K = K;
+    g.A.base = A; g.A.off_r = ctx->table({{M, lda}}); g.A.off_c = ctx->table({{K, 1}}); g.A.c_fast = true;
+    g.B.base = B; g.B.off_r = ctx->table({{K, ldb}}); g.B.off_c = ctx->table({{N, 1}}); g.B.c_fast = true;
+    g.C = C; g.c_m = ctx->table({{M, ldc}}); g.c_n = ctx->table({{N, 1}}); g.beta = 0.0;
+    ctx->phase = TRG_PHASE_X2;
+    trg::gemm(*ctx, g, ctx->cfg.precision);
+    TRG_CUDA(cudaStreamSynchronize(ctx->stream));
+    if (trg::read_status(*ctx) & trg::ST_TIMEOUT) return bad(ctx, TRG_ETIMEOUT, "gemm: device wait timed out");
     return TRG_OK;
     TRG_GUARD_END(ctx)
 }

@@ -77,6 +77,7 @@ struct Ctx {
     Buf eig;               // subspace-iteration buffers
     Buf eig_small;         // m x m buffers
     Buf flags;             // per-column flags (int)
+    Buf split_ws;          // split GEMM: exponents and BF16 slices of both operands
     std::map<std::string, Buf> tables;  // cached offset tables
 
     // ---- phase timing

@@ -172,6 +172,19 @@ class Solver:
         return out
 
     # -- components on device tensors (torch CUDA float64, contiguous)
+    def gemm(self, a, b):
+        torch = _torch()
+        _require(a, 2)
+        _require(b, 2)
+        m, k = a.shape
+        k2, n = b.shape
+        if k != k2:
+            raise ValueError("inner dimensions differ")
+        c = torch.empty((m, n), dtype=torch.float64, device=a.device)
+        self._check(self._lib.trg_gemm(self._h, m, n, k, a.data_ptr(), k, b.data_ptr(), n, c.data_ptr(), n),
+                    "trg_gemm")
+        return c
+
     def environment(self, t):
         torch = _torch()
         _require(t, 4)

@@ -84,10 +84,13 @@ def test_isometry_untruncated_is_identity(torch):
 
 
 # ----------------------------------------------------------- full solves ---
+GAP_PINNED = 1e-6   # spectra are compared only while every earlier cut had this relative gap
+
+
 @pytest.mark.parametrize("name", sorted(GOLDEN))
 def test_solve_matches_oracle(torch, name):
     g = GOLDEN[name]
-    with _solver(trunc=g["trunc"]) as s:
+    with _solver(trunc=g["trunc"], eig_tol=1e-13) as s:
         s.init_tensor(g["model"], g["beta"], g["h"])
         s.coarse_grain(g["dcut"], g["nsteps"])
         f, lnz = s.free_energy()
@@ -95,13 +98,24 @@ def test_solve_matches_oracle(torch, name):
         _, dx, dy, _ = s.state()
     assert [dx, dy] == g["steps"][-1]["dims"]
     assert abs(f - g["f"]) <= F_TOL_FP64, (f, g["f"])
+    compared = 0
     for st, lam in zip(g["steps"], spectra):
         if not st["truncated"]:
             assert lam.size == 0
             continue
         ref = np.array(st["kept"])
         assert lam.size == ref.size
-        assert np.abs(lam - ref).max() <= SPEC_TOL * ref[0], st["step"]
+        # after a cut with a tiny gap the kept vectors are fixed only to about
+        # residual / gap, and later spectra inherit that: stop comparing there
+        # (f above stays pinned for the whole solve)
+        if compared and prev_gap < GAP_PINNED:
+            break
+        prev_gap = st["gap"]
+        compared += 1
+        # max|T| depends on the gauge of the legs (untruncated steps use U = I
+        # here and eigenvectors in the oracle), and M is quartic in T, so the
+        # spectra agree up to one positive factor: compare lam_i / lam_1
+        assert np.abs(lam / lam[0] - ref / ref[0]).max() <= SPEC_TOL, st["step"]
 
 
 @pytest.mark.parametrize("key", sorted(TORI))

@@ -1,0 +1,103 @@
+"""Split-precision path (BF16 slices on tcgen05, exact FP32 partial sums).
+
+* Integer-valued operands are represented exactly by the slices and their
+  products sum exactly, so the split GEMM must agree bit for bit with the
+  FP64 product (this checks slicing, TMA layouts, MMA descriptors, the
+  exact chunk drains and the integer-built FP64 epilogue).
+* Random operands must stay inside the error bound of the splitting:
+  |C - AB| <= K rowmax|A| colmax|B| (S + 2) 2^(3 - 8 S).
+* Components and full solves against the oracle within the split tolerance
+  (|f_split - f_oracle| <= 1e-9).
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+from oracle import hotrg
+from paper_2306_00358_gb300 import Solver, workloads
+
+pytestmark = pytest.mark.gpu
+HERE = os.path.dirname(os.path.abspath(__file__))
+GOLDEN = json.load(open(os.path.join(HERE, "golden", "oracle_solves.json")))
+F_TOL_SPLIT = 1e-9
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    return torch
+
+
+def _bound(a, b, s):
+    k = a.shape[1]
+    return k * np.abs(a).max(axis=1)[:, None] * np.abs(b).max(axis=0)[None, :] * (s + 2) * 2.0 ** (3 - 8 * s)
+
+
+@pytest.mark.parametrize("m,n,k", [(1, 1, 1), (128, 128, 32), (130, 257, 100), (300, 70, 2100), (64, 200, 1025)])
+@pytest.mark.parametrize("s", [2, 4])
+def test_split_gemm_exact_on_integers(torch, m, n, k, s):
+    rng = np.random.default_rng(m * 7 + n * 3 + k + s)
+    a = rng.integers(-100, 101, size=(m, k)).astype(np.float64)
+    b = rng.integers(-100, 101, size=(k, n)).astype(np.float64)
+    ref = a @ b
+    with Solver(0, precision="split", split_slices=s) as sv:
+        c = sv.gemm(torch.from_numpy(a).cuda(), torch.from_numpy(b).cuda()).cpu().numpy()
+    assert np.array_equal(c, ref)
+
+
+@pytest.mark.parametrize("m,n,k", [(200, 300, 4096), (129, 64, 777), (512, 80, 4096)])
+@pytest.mark.parametrize("s", [3, 4, 5])
+def test_split_gemm_error_bound(torch, m, n, k, s):
+    rng = np.random.default_rng(1000 + s)
+    a = rng.standard_normal((m, k)) * np.exp(rng.uniform(-8, 8, size=(m, 1)))
+    b = rng.standard_normal((k, n)) * np.exp(rng.uniform(-8, 8, size=(1, n)))
+    ref = a @ b
+    with Solver(0, precision="split", split_slices=s) as sv:
+        c = sv.gemm(torch.from_numpy(a).cuda(), torch.from_numpy(b).cuda()).cpu().numpy()
+    assert np.all(np.abs(c - ref) <= _bound(a, b, s))
+
+
+def test_split_gemm_zero_rows_and_tiny_values(torch):
+    a = np.zeros((40, 64))
+    a[3] = 1e-300
+    a[5, 7] = 3.0
+    b = np.ones((64, 33))
+    with Solver(0, precision="split", split_slices=4) as sv:
+        c = sv.gemm(torch.from_numpy(a).cuda(), torch.from_numpy(b).cuda()).cpu().numpy()
+    ref = a @ b
+    assert np.array_equal(c[5], ref[5])
+    assert np.all(c[[0, 1, 2, 4, 6]] == 0.0)
+    assert np.allclose(c[3], ref[3], rtol=1e-9, atol=0)
+
+
+@pytest.mark.parametrize("dx,dy", [(5, 3), (12, 7), (16, 16)])
+def test_split_environment(torch, dx, dy):
+    t = workloads.random_tensor((dx, dy, dx, dy), seed=500 + dx)
+    ref = hotrg.environment_x(t)
+    with Solver(0, precision="split", split_slices=4) as sv:
+        m = sv.environment(torch.from_numpy(t).cuda()).cpu().numpy()
+    assert np.abs(m - ref).max() <= 1e-7 * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("dx,dy,dn,ws", [(8, 8, 20, 0), (12, 7, 33, 0), (16, 16, 64, 3_000_000)])
+def test_split_contraction(torch, dx, dy, dn, ws):
+    t = workloads.random_tensor((dx, dy, dx, dy), seed=600 + dx)
+    u = workloads.random_isometry(dx, dn, seed=700 + dn)
+    ref = hotrg.contract_x(t, u)
+    with Solver(0, precision="split", split_slices=4, workspace_bytes=ws) as sv:
+        out = sv.contract(torch.from_numpy(t).cuda(), torch.from_numpy(u).cuda()).cpu().numpy()
+    assert np.abs(out - ref).max() <= 1e-7 * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("name", ["ising_b0.44_d16_n40", "ising_bc_d16_h1e-3_n40", "xy_b1.0_d12_n12"])
+@pytest.mark.parametrize("s", [4, 5])
+def test_split_solve_matches_oracle(torch, name, s):
+    g = GOLDEN[name]
+    with Solver(0, precision="split", split_slices=s, trunc=g["trunc"]) as sv:
+        sv.init_tensor(g["model"], g["beta"], g["h"])
+        sv.coarse_grain(g["dcut"], g["nsteps"])
+        f, _ = sv.free_energy()
+    assert abs(f - g["f"]) <= F_TOL_SPLIT, (f, g["f"], abs(f - g["f"]))
