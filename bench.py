@@ -43,6 +43,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--solve", action="store_true", help="also time one full 40-half-step solve")
+    ap.add_argument("--gemm", type=int, nargs=3, metavar=("M", "N", "K"), default=None,
+                    help="micro-benchmark one split GEMM of this size instead of the half-step")
     return ap.parse_args()
 
 
@@ -282,8 +284,45 @@ def run_native(args):
         dist.destroy_process_group()
 
 
+def run_gemm(args):
+    """Time C = A B (FP64 operands, split precision) through trg_gemm."""
+    import numpy as np
+    import torch
+
+    from paper_2306_00358_gb300 import Solver
+
+    m, n, k = args.gemm
+    precision = args.precision or "split"
+    steps = args.steps or 5
+    rng = np.random.default_rng(3)
+    a = torch.from_numpy(rng.standard_normal((m, k))).cuda()
+    b = torch.from_numpy(rng.standard_normal((k, n))).cuda()
+    s = Solver(0, precision=precision, split_slices=args.slices)
+    for _ in range(max(1, args.warmup)):
+        s.gemm(a, b)
+    s.profile(True)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        s.gemm(a, b)
+    torch.cuda.synchronize()
+    wall = (time.perf_counter() - t0) / steps
+    ph = s.phase_stats()
+    mma = ph["mma"]
+    line = {"mode": "gemm", "m": m, "n": n, "k": k, "precision": precision, "slices": args.slices,
+            "seconds_per_gemm": wall, "fp64_equiv_tflops": 2.0 * m * n * k / wall / 1e12}
+    if mma["calls"]:
+        t = mma["ms"] / mma["calls"] / 1e3
+        line.update({"mma_ms": t * 1e3, "mma_tflops": mma["mma_flops"] / mma["calls"] / t / 1e12})
+    print(json.dumps(line), flush=True)
+    s.close()
+
+
 def main():
     args = parse()
+    if args.gemm:
+        run_gemm(args)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:

@@ -324,7 +324,7 @@ static void orthonormalise(Ctx& ctx, double* Y, int64_t n, int m, double* G, dou
             k_rand_cols<<<grid, 256, 0, ctx.stream>>>(Y, n, m, flags, seed, ++salt);
             TRG_LAUNCHED(ctx);
         }
-        k_trsm_rows<<<(unsigned)((n + 127) / 128), 128, smem, ctx.stream>>>(Y, L, n, m);
+        k_trsm_rows<<<(unsigned)((n + 31) / 32), 32, smem, ctx.stream>>>(Y, L, n, m);
         TRG_LAUNCHED(ctx);
     }
 }
@@ -366,6 +366,18 @@ int isometry(Ctx& ctx, const double* M, int64_t n, int dcut, double* U, std::vec
         TRG_LAUNCHED(ctx);
     }
     orthonormalise(ctx, Q, n, m, G, L, flags, nbad, seed, salt);
+    // two plain block power steps before the first Rayleigh-Ritz: the random
+    // start is mostly noise, and the Jacobi solve of a dense H is the costly part
+    for (int pre = 0; pre < 2 && m < n; ++pre) {
+        GemmDesc g;
+        g.M = n; g.N = m; g.K = n;
+        g.A.base = M; g.A.off_r = ctx.table({{n, n}}); g.A.off_c = ctx.table({{n, 1}}); g.A.c_fast = true;
+        g.B.base = Q; g.B.off_r = ctx.table({{n, 1}}); g.B.off_c = ctx.table({{m, n}}); g.B.c_fast = false;
+        g.C = Y; g.c_m = ctx.table({{n, 1}}); g.c_n = ctx.table({{m, n}}); g.beta = 0.0;
+        gemm(ctx, g, precision);
+        std::swap(Q, Y);
+        orthonormalise(ctx, Q, n, m, G, L, flags, nbad, seed, salt);
+    }
 
     const size_t jac_smem = (size_t)m * m * 8 + (m + 2) * 8 + (m + 2) * 4;
     // Split products carry ~2^-(8S-1) relative error, which floors the Ritz

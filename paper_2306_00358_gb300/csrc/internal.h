@@ -78,6 +78,7 @@ struct Ctx {
     Buf eig_small;         // m x m buffers
     Buf flags;             // per-column flags (int)
     Buf split_ws;          // split GEMM: exponents and BF16 slices of both operands
+    Buf f64_partial;       // FP64 GEMM: split-K partial sums
     std::map<std::string, Buf> tables;  // cached offset tables
 
     // ---- phase timing
