@@ -369,8 +369,14 @@ k_split_mma(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
                     for (int h = 0; h < 2; ++h) {
                         const uint32_t col = (uint32_t)(colh * 64 + h * 32);
                         uint32_t r[32];
-                        tmem_ld32(tmem + lane_base + 384 + col, r);
-                        tmem_wait_ld();
+                        if (S >= 3) {
+                            tmem_ld32(tmem + lane_base + 384 + col, r);
+                            tmem_wait_ld();
+                        } else {
+                            // two slices: no product lands in ACCR, whose columns are never written
+#pragma unroll
+                            for (int j = 0; j < 32; ++j) r[j] = 0u;
+                        }
                         const int n0 = nb * BN + (int)col;
 #pragma unroll
                         for (int j = 0; j < 32; ++j) {

@@ -49,7 +49,7 @@ def test_split_gemm_exact_on_integers(torch, m, n, k, s):
 
 
 @pytest.mark.parametrize("m,n,k", [(200, 300, 4096), (129, 64, 777), (512, 80, 4096)])
-@pytest.mark.parametrize("s", [3, 4, 5])
+@pytest.mark.parametrize("s", [2, 3, 4, 5])
 def test_split_gemm_error_bound(torch, m, n, k, s):
     rng = np.random.default_rng(1000 + s)
     a = rng.standard_normal((m, k)) * np.exp(rng.uniform(-8, 8, size=(m, 1)))
