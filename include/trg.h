@@ -190,6 +190,32 @@ int trg_contract(trg_ctx* ctx, const double* t_dev, const double* U_dev,
 int trg_gemm(trg_ctx* ctx, int M, int N, int K, const double* A_dev, int lda, const double* B_dev, int ldb,
              double* C_dev, int ldc);
 
+/*
+ * Allocation-free split-precision product C = A B (no counterpart in the
+ * paper; an addition for callers that must not allocate device memory while
+ * they run -- e.g. a serving process that handed all memory to its own pool
+ * at start-up, or code where a cudaMalloc would synchronise the device -- and
+ * for callers that hold no context).
+ *
+ * Same arithmetic and layouts as trg_gemm in TRG_SPLIT_BF16 mode with
+ * `slices` BF16 slices (2..5), on the CURRENT CUDA device and on `stream`
+ * (a cudaStream_t, NULL = default stream).  It calls no cudaMalloc, cudaFree
+ * or other allocating routine: its scratch (offset tables, exponents, slices,
+ * a status word) is a fixed 64 MiB device array inside the library, held by
+ * every GPU that loads the library until the process exits.  Sizes whose
+ * scratch exceeds 64 MiB -- about S*(M+N)*K*2 bytes plus 16*(M+N+K) -- are
+ * rejected with TRG_EINVAL (use trg_gemm for them).
+ *   - The first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress); make that first call before any stream capture.
+ *   - Every call shares the one array: calls that overlap on the GPU (other
+ *     threads, other streams) race and corrupt each other's results.  The
+ *     call waits for its own work to finish before returning.
+ * Returns TRG_OK, TRG_EINVAL, TRG_ENOTSUP (not a GB300), TRG_ETIMEOUT or
+ * TRG_ECUDA.
+ */
+int trg_gemm_noalloc(int M, int N, int K, const double* A_dev, int lda, const double* B_dev, int ldb,
+                     double* C_dev, int ldc, int slices, void* stream);
+
 /* ------------------------------------------------------- profiling ----- */
 /* Phases of a half-step, timed with CUDA events on the context's stream. */
 typedef enum trg_phase {

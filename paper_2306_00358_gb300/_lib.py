@@ -66,6 +66,8 @@ SIGNATURES = {
     "trg_isometry": (c_int, [c_void_p, c_void_p, c_int, c_int, c_void_p, P_double, P_int]),
     "trg_contract": (c_int, [c_void_p, c_void_p, c_void_p, c_int, c_int, c_int, c_void_p]),
     "trg_gemm": (c_int, [c_void_p, c_int, c_int, c_int, c_void_p, c_int, c_void_p, c_int, c_void_p, c_int]),
+    "trg_gemm_noalloc": (c_int, [c_int, c_int, c_int, c_void_p, c_int, c_void_p, c_int, c_void_p, c_int, c_int,
+                                 c_void_p]),
     "trg_profile_enable": (c_int, [c_void_p, c_int]),
     "trg_profile_read": (c_int, [c_void_p, c_int, ctypes.POINTER(trg_phase_stats)]),
     "trg_status_string": (ctypes.c_char_p, [c_int]),

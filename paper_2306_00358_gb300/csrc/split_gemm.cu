@@ -32,6 +32,7 @@
 
 #include <algorithm>
 #include <cstring>
+#include <mutex>
 
 #include "internal.h"
 
@@ -618,4 +619,157 @@ void gemm_split(Ctx& ctx, const GemmDesc& d) {
     ctx.region_end(tok, 2.0 * (double)M * N * K, products * 2.0 * (double)M * N * Kp);
 }
 
+// ----------------------------------------------------------------------------
+// Allocation-free variant of the split GEMM (trg_gemm_noalloc).
+//
+// For callers that must not allocate device memory while they run: code that
+// has already handed all device memory to its own pool (a serving process
+// that sized its arena at start-up), code running where a cudaMalloc would
+// synchronise the device or is not permitted, and code that cannot own a
+// context object.  Its scratch -- offset tables, scale exponents, BF16 slices
+// and the status word -- lives in one file-scope device array of fixed size,
+// which every GPU that loads the library holds until the process exits.
+// ----------------------------------------------------------------------------
+namespace {
+
+constexpr size_t NOALLOC_BYTES = (size_t)64 << 20;   // 64 MiB
+__device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_BYTES];
+
+// The array's name is a host-side stand-in in host code; the device address
+// comes from cudaGetSymbolAddress, once per device, with that device current.
+constexpr int MAX_DEVICES = 64;
+std::mutex g_noalloc_mu;
+void* g_noalloc_ptr[MAX_DEVICES] = {};
+int g_noalloc_sms[MAX_DEVICES] = {};
+
+__global__ void k_affine_table(int64_t* t, int64_t n, int64_t stride) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) t[i] = i * stride;
+}
+
+size_t round256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+}  // namespace
+
 }  // namespace trg
+
+extern "C" int trg_gemm_noalloc(int M, int N, int K, const double* A, int lda, const double* B, int ldb,
+                                double* C, int ldc, int slices, void* stream_ptr) {
+    using namespace trg;
+    if (!A || !B || !C || M < 1 || N < 1 || K < 1 || lda < K || ldb < N || ldc < N) return TRG_EINVAL;
+    if (slices < 2 || slices > 5 || K > (1 << 17)) return TRG_EINVAL;
+    const int S = slices;
+    const int Mp = (M + BM - 1) / BM * BM, Np = (N + BN - 1) / BN * BN, Kp = (K + BK - 1) / BK * BK;
+    // layout of the scratch array
+    const size_t o_am = 0;
+    const size_t o_ak = o_am + round256((size_t)M * 8);
+    const size_t o_bk = o_ak + round256((size_t)K * 8);
+    const size_t o_bn = o_bk + round256((size_t)K * 8);
+    const size_t o_cm = o_bn + round256((size_t)N * 8);
+    const size_t o_cn = o_cm + round256((size_t)M * 8);
+    const size_t o_st = o_cn + round256((size_t)N * 8);
+    const size_t o_ea = o_st + 256;
+    const size_t o_eb = o_ea + round256((size_t)Mp * 4);
+    const size_t o_sa = o_eb + round256((size_t)Np * 4);
+    const size_t o_sb = o_sa + round256((size_t)S * Mp * Kp * 2);
+    const size_t total = o_sb + round256((size_t)S * Np * Kp * 2);
+    if (total > NOALLOC_BYTES) return TRG_EINVAL;   // beyond the fixed scratch: use trg_gemm
+
+    cudaStream_t stream = (cudaStream_t)stream_ptr;
+    try {
+        int dev = 0;
+        TRG_CUDA(cudaGetDevice(&dev));
+        if (dev < 0 || dev >= MAX_DEVICES) return TRG_ENOTSUP;
+        unsigned char* base;
+        int sms;
+        {
+            std::lock_guard<std::mutex> lock(g_noalloc_mu);
+            if (!g_noalloc_ptr[dev]) {
+                cudaDeviceProp prop;
+                TRG_CUDA(cudaGetDeviceProperties(&prop, dev));
+                if (prop.major != 10 || prop.minor != 3) return TRG_ENOTSUP;
+                void* p = nullptr;
+                const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+                if (e != cudaSuccess || !p) return TRG_ECUDA;
+                g_noalloc_sms[dev] = prop.multiProcessorCount;
+                g_noalloc_ptr[dev] = p;
+            }
+            base = (unsigned char*)g_noalloc_ptr[dev];
+            sms = g_noalloc_sms[dev];
+        }
+        int64_t* am = (int64_t*)(base + o_am);
+        int64_t* ak = (int64_t*)(base + o_ak);
+        int64_t* bk = (int64_t*)(base + o_bk);
+        int64_t* bn = (int64_t*)(base + o_bn);
+        int64_t* cm = (int64_t*)(base + o_cm);
+        int64_t* cn = (int64_t*)(base + o_cn);
+        int* status = (int*)(base + o_st);
+        int* ea = (int*)(base + o_ea);
+        int* eb = (int*)(base + o_eb);
+        uint16_t* sa = (uint16_t*)(base + o_sa);
+        uint16_t* sb = (uint16_t*)(base + o_sb);
+
+        // the array keeps the previous call's contents: rebuild the tables,
+        // clear the status word and the exponents (maxima start from zero)
+        const struct { int64_t* t; int64_t n, s; } tabs[6] = {
+            {am, M, lda}, {ak, K, 1}, {bk, K, ldb}, {bn, N, 1}, {cm, M, ldc}, {cn, N, 1}};
+        for (const auto& tb : tabs) {
+            k_affine_table<<<(unsigned)((tb.n + 255) / 256), 256, 0, stream>>>(tb.t, tb.n, tb.s);
+            TRG_CUDA(cudaGetLastError());
+        }
+        TRG_CUDA(cudaMemsetAsync(status, 0, sizeof(int), stream));
+        TRG_CUDA(cudaMemsetAsync(ea, 0, (size_t)M * sizeof(int), stream));
+        TRG_CUDA(cudaMemsetAsync(eb, 0, (size_t)N * sizeof(int), stream));
+
+        // row exponents and slices of A (rows m, k contiguous) and of B as (n, k)
+        {
+            dim3 ga((unsigned)((K + SL_K - 1) / SL_K), (unsigned)((M + SL_R - 1) / SL_R));
+            k_row_exponent<<<ga, 256, 0, stream>>>(A, am, ak, M, K, 1, ea);
+            dim3 gb((unsigned)((K + SL_K - 1) / SL_K), (unsigned)((N + SL_R - 1) / SL_R));
+            k_row_exponent<<<gb, 256, 0, stream>>>(B, bn, bk, N, K, 0, eb);
+            k_exponent_finish<<<(unsigned)((M + 255) / 256), 256, 0, stream>>>(ea, M);
+            k_exponent_finish<<<(unsigned)((N + 255) / 256), 256, 0, stream>>>(eb, N);
+            TRG_CUDA(cudaGetLastError());
+            dim3 sa_grid((unsigned)((Kp + SL_K - 1) / SL_K), (unsigned)(Mp / SL_R));
+            dim3 sb_grid((unsigned)((Kp + SL_K - 1) / SL_K), (unsigned)(Np / SL_R));
+            switch (S) {
+                case 2: k_slice<2><<<sa_grid, 256, 0, stream>>>(A, am, ak, M, K, Mp, Kp, 1, ea, sa);
+                        k_slice<2><<<sb_grid, 256, 0, stream>>>(B, bn, bk, N, K, Np, Kp, 0, eb, sb); break;
+                case 3: k_slice<3><<<sa_grid, 256, 0, stream>>>(A, am, ak, M, K, Mp, Kp, 1, ea, sa);
+                        k_slice<3><<<sb_grid, 256, 0, stream>>>(B, bn, bk, N, K, Np, Kp, 0, eb, sb); break;
+                case 4: k_slice<4><<<sa_grid, 256, 0, stream>>>(A, am, ak, M, K, Mp, Kp, 1, ea, sa);
+                        k_slice<4><<<sb_grid, 256, 0, stream>>>(B, bn, bk, N, K, Np, Kp, 0, eb, sb); break;
+                default: k_slice<5><<<sa_grid, 256, 0, stream>>>(A, am, ak, M, K, Mp, Kp, 1, ea, sa);
+                         k_slice<5><<<sb_grid, 256, 0, stream>>>(B, bn, bk, N, K, Np, Kp, 0, eb, sb); break;
+            }
+            TRG_CUDA(cudaGetLastError());
+        }
+        const CUtensorMap ta = make_map(sa, S * Mp, Kp);
+        const CUtensorMap tbm = make_map(sb, S * Np, Kp);
+        MmaArgs a;
+        a.M = M; a.N = N; a.Kp = Kp; a.Mp = Mp; a.Np = Np; a.S = S;
+        a.ea = ea; a.eb = eb; a.C = C; a.c_m = cm; a.c_n = cn; a.status = status;
+        const int tiles = ((M + BM - 1) / BM) * ((N + BN - 1) / BN);
+        const int grid = std::max(1, std::min(tiles, sms));
+        switch (S) {
+#define TRG_NOALLOC_MMA(SS)                                                                                  \
+    TRG_CUDA(cudaFuncSetAttribute(k_split_mma<SS>, cudaFuncAttributeMaxDynamicSharedMemorySize,              \
+                                  smem_bytes_for(SS)));                                                      \
+    k_split_mma<SS><<<grid, THREADS, smem_bytes_for(SS), stream>>>(ta, tbm, a);                              \
+    break;
+            case 2: TRG_NOALLOC_MMA(2)
+            case 3: TRG_NOALLOC_MMA(3)
+            case 4: TRG_NOALLOC_MMA(4)
+            default: TRG_NOALLOC_MMA(5)
+#undef TRG_NOALLOC_MMA
+        }
+        TRG_CUDA(cudaGetLastError());
+        int st = 0;
+        TRG_CUDA(cudaMemcpyAsync(&st, status, sizeof(int), cudaMemcpyDeviceToHost, stream));
+        TRG_CUDA(cudaStreamSynchronize(stream));
+        if (st & ST_TIMEOUT) return TRG_ETIMEOUT;
+        return TRG_OK;
+    } catch (const Error& e) {
+        return e.status;
+    }
+}
