@@ -45,6 +45,10 @@ def parse():
     ap.add_argument("--solve", action="store_true", help="also time one full 40-half-step solve")
     ap.add_argument("--gemm", type=int, nargs=3, metavar=("M", "N", "K"), default=None,
                     help="micro-benchmark one split GEMM of this size instead of the half-step")
+    ap.add_argument("--sweep", action="store_true", help="FP64 vs split solves over couplings (accuracy)")
+    ap.add_argument("--betas", default=None)
+    ap.add_argument("--fields", default=None)
+    ap.add_argument("--dcuts", default=None)
     return ap.parse_args()
 
 
@@ -194,6 +198,7 @@ def run_native(args):
     barrier()
     s.profile(True)
     launches0 = s.launch_count()
+    counters0 = s.counters()
     clocks = ClockSampler(local)
     clocks.start()
     ev0 = torch.cuda.Event(enable_timing=True)
@@ -206,6 +211,7 @@ def run_native(args):
     clk = clocks.stop()
     ms = ev0.elapsed_time(ev1)
     launches = s.launch_count() - launches0
+    counters = {k: v - counters0[k] for k, v in s.counters().items()}
     ph = s.phase_stats()
     s.profile(False)
     t_max = torch.tensor([ms], dtype=torch.float64, device="cuda")
@@ -277,7 +283,7 @@ def run_native(args):
                            "l2": "inputs larger than L2 (T 134 MB, M 134 MB, workspace >= 1 GB per step)",
                            "parallelism": "replicas" if world > 1 else "single"},
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
-                "phases_ms": {k: round(v["ms"], 3) for k, v in ph.items()}, "solve": solve}
+                "phases_ms": {k: round(v["ms"], 3) for k, v in ph.items()}, "counters": counters, "solve": solve}
         print(json.dumps(line), flush=True)
     s.close()
     if world > 1:
@@ -318,10 +324,66 @@ def run_gemm(args):
     s.close()
 
 
+def onsager_f(beta):
+    """Exact Ising free energy at h = 0 (single-integral form, composite
+    Gauss-Legendre graded towards pi/2); used only to report |f - f_exact|."""
+    import numpy as np
+    c2 = math.cosh(2 * beta)
+    k2 = (2 * math.sinh(2 * beta) / (c2 * c2)) ** 2
+    x, w = np.polynomial.legendre.leggauss(40)
+    half = 0.5 * math.pi
+    edges = [0.0] + [half - half * 0.5 ** i for i in range(1, 61)] + [half]
+    tot = 0.0
+    for a, b in zip(edges[:-1], edges[1:]):
+        p = 0.5 * (a + b) + 0.5 * (b - a) * x
+        s = np.sin(p)
+        tot += 0.5 * (b - a) * float(np.sum(w * np.log(0.5 * (1 + np.sqrt(np.maximum(0, 1 - k2 * s * s))))))
+    return -(math.log(2 * c2) + 2 * tot / (2 * math.pi)) / beta
+
+
+def run_sweep(args):
+    """Coupling sweep: FP64 and split solves of 40 half-steps; reports
+    |f_split - f_fp64| for every run and |f - f_exact| at h = 0."""
+    import torch
+
+    from paper_2306_00358_gb300 import Solver
+
+    betas = [float(b) for b in args.betas.split(",")] if args.betas else [BETA_C, 0.40, 0.48]
+    fields = [float(h) for h in args.fields.split(",")] if args.fields else [0.0, 1e-3]
+    dcuts = [int(d) for d in args.dcuts.split(",")] if args.dcuts else [32, 48, 64]
+    out = []
+    for dcut in dcuts:
+        for beta in betas:
+            for h in fields:
+                rec = {"beta": beta, "h": h, "dcut": dcut}
+                for prec, slices in (("fp64", 4), ("split", args.slices)):
+                    torch.cuda.synchronize()
+                    t0 = time.perf_counter()
+                    with Solver(0, precision=prec, split_slices=slices) as s:
+                        s.init_tensor("ising", beta, h)
+                        s.coarse_grain(dcut, 40)
+                        f, _ = s.free_energy()
+                    rec[f"f_{prec}"] = f
+                    rec[f"seconds_{prec}"] = time.perf_counter() - t0
+                rec["abs_df_split_fp64"] = abs(rec["f_split"] - rec["f_fp64"])
+                if h == 0.0:
+                    fe = onsager_f(beta)
+                    rec["f_exact"] = fe
+                    rec["rel_err_fp64"] = abs(rec["f_fp64"] - fe) / abs(fe)
+                    rec["rel_err_split"] = abs(rec["f_split"] - fe) / abs(fe)
+                print(json.dumps(rec), flush=True)
+                out.append(rec)
+    print(json.dumps({"mode": "sweep", "slices": args.slices, "runs": len(out),
+                      "max_abs_df_split_fp64": max(r["abs_df_split_fp64"] for r in out)}), flush=True)
+
+
 def main():
     args = parse()
     if args.gemm:
         run_gemm(args)
+        return
+    if args.sweep:
+        run_sweep(args)
         return
     if args.impl == "reference":
         run_reference(args)

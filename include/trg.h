@@ -68,7 +68,8 @@ typedef struct trg_config {
     int split_slices;        /* BF16 slices per operand in TRG_SPLIT_BF16, 2..5 (default 4) */
     int split_from_step;     /* half-steps with index < this run in FP64 (default 0) */
     int trunc;               /* trg_trunc (default TRG_TRUNC_PAPER) */
-    double gap_tol;          /* multiplet gap, relative to lambda_1 (default 1e-8) */
+    double gap_tol;          /* multiplet gap, relative to lambda_1 (default 1e-6; in
+                                TRG_SPLIT_BF16 at least 2^-(8*split_slices-12)) */
     int oversample;          /* subspace-iteration oversampling p (default 16) */
     double eig_tol;          /* Ritz residual tolerance relative to lambda_1 (default 1e-12; in
                                 TRG_SPLIT_BF16 at least 2^-(8*split_slices-10)) */
@@ -242,6 +243,11 @@ int trg_profile_enable(trg_ctx* ctx, int on);
 
 /* Synchronise the stream and read the accumulated statistics of a phase. */
 int trg_profile_read(trg_ctx* ctx, int phase, trg_phase_stats* out);
+
+/* Diagnostic counters since trg_create: out[0] subspace iterations,
+ * out[1] Rayleigh-Ritz solves, out[2] FP32 Jacobi sweeps, out[3] FP64
+ * Jacobi sweeps, out[4] Cholesky-QR column repairs; n <= 8 entries. */
+int trg_get_counters(const trg_ctx* ctx, uint64_t* out, int n);
 
 /* ------------------------------------------------------------ misc ----- */
 const char* trg_status_string(int status);

@@ -32,7 +32,8 @@ Readings where the paper is silent or ambiguous (each is a keyword here):
     the signed max once per full x+y iteration as the listing does ("paper");
   * truncation "paper" keeps exactly min(Dx^2, Dcut) vectors; "multiplet"
     lowers Dn until the relative gap (lam[Dn-1] - lam[Dn]) / lam[0] is at
-    least gap_tol, so that a degenerate multiplet is never split.
+    least gap_tol (default 1e-6), so that a degenerate multiplet is never
+    split.
 """
 from __future__ import annotations
 
@@ -61,7 +62,7 @@ def environment_x(t: np.ndarray) -> np.ndarray:
 
 
 def truncation_dim(lam: np.ndarray, dcut: int, trunc: str = "paper",
-                   gap_tol: float = 1e-8) -> int:
+                   gap_tol: float = 1e-6) -> int:
     """Number of kept vectors: min(size, Dcut) as the SVD helper of the
     listing does; with trunc="multiplet", lowered until the cut does not split
     a (near-)degenerate multiplet."""
@@ -78,7 +79,7 @@ def truncation_dim(lam: np.ndarray, dcut: int, trunc: str = "paper",
     return k
 
 
-def isometry(m: np.ndarray, dcut: int, trunc: str = "paper", gap_tol: float = 1e-8):
+def isometry(m: np.ndarray, dcut: int, trunc: str = "paper", gap_tol: float = 1e-6):
     """Leading eigenvectors of the symmetrised environment matrix.
 
     Returns (U, lam_all) with U of shape (Dx, Dx, Dn) (first index: the leg of
@@ -138,7 +139,7 @@ class HalfStep:
 
 
 def half_step(t: np.ndarray, dcut: int, direction: str, trunc: str = "paper",
-              gap_tol: float = 1e-8) -> HalfStep:
+              gap_tol: float = 1e-6) -> HalfStep:
     """One directional blocking (x: stack vertically; y: stack horizontally)."""
     if direction == "x":
         m = environment_x(t)
@@ -173,7 +174,7 @@ class Solve:
 
 
 def solve(t0: np.ndarray, beta: float, dcut: int, nsteps: int, trunc: str = "paper",
-          gap_tol: float = 1e-8, norm: str = "halfstep", keep_full_spectra: bool = False,
+          gap_tol: float = 1e-6, norm: str = "halfstep", keep_full_spectra: bool = False,
           first_direction: str = "x") -> Solve:
     """Run nsteps alternating half-steps (x first) from the raw tensor t0 and
     return ln Z / V and f = -(ln Z / V) / beta for the periodic lattice of

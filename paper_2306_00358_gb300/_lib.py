@@ -73,6 +73,7 @@ SIGNATURES = {
     "trg_status_string": (ctypes.c_char_p, [c_int]),
     "trg_last_error": (ctypes.c_char_p, [c_void_p]),
     "trg_launch_count": (c_uint64, [c_void_p]),
+    "trg_get_counters": (c_int, [c_void_p, ctypes.POINTER(c_uint64), c_int]),
 }
 
 _lock = threading.Lock()

@@ -233,7 +233,7 @@ int trg_config_default(trg_config* cfg) {
     cfg->split_slices = 4;
     cfg->split_from_step = 0;
     cfg->trunc = TRG_TRUNC_PAPER;
-    cfg->gap_tol = 1e-8;
+    cfg->gap_tol = 1e-6;
     cfg->oversample = 16;
     cfg->eig_tol = 1e-12;
     cfg->eig_max_iter = 300;
@@ -555,5 +555,11 @@ const char* trg_status_string(int status) {
 const char* trg_last_error(const trg_ctx* ctx) { return ctx ? ctx->last_error.c_str() : ""; }
 
 uint64_t trg_launch_count(const trg_ctx* ctx) { return ctx ? ctx->launches : 0; }
+
+int trg_get_counters(const trg_ctx* ctx, uint64_t* out, int n) {
+    if (!ctx || !out || n < 0 || n > 8) return TRG_EINVAL;
+    for (int i = 0; i < n; ++i) out[i] = ctx->counters[i];
+    return TRG_OK;
+}
 
 }  // extern "C"

@@ -87,114 +87,163 @@ __global__ void __launch_bounds__(256) k_col_normalize(double* Y, int64_t n, int
     for (int64_t r = threadIdx.x; r < n; r += 256) y[r] *= scale;
 }
 
-// Left-looking Cholesky G = L L^T of an m x m Gram matrix of unit columns.
-// A pivot d_j <= tau * G_jj marks column j as dependent (flags[j] = 1,
-// *nbad += 1); it is replaced by G_jj so the factorisation can continue.
+// Right-looking Cholesky G = L L^T of an m x m Gram matrix of unit columns
+// (the trailing updates run in parallel; FP64 latency, not throughput, is what
+// a column-at-a-time dot product would pay for).  A pivot d_j <= tau * G_jj
+// marks column j as dependent (flags[j] = 1, *nbad += 1); the pivot is then
+// replaced by G_jj so the factorisation can continue.
 __global__ void __launch_bounds__(256) k_chol_flag(const double* G, double* Lout, int m, double tau,
                                                    int* flags, int* nbad) {
-    extern __shared__ double L[];   // m*m, row-major
-    __shared__ double red[33];
-    for (int e = threadIdx.x; e < m * m; e += 256) L[e] = 0.0;
+    extern __shared__ double L[];   // m*m, row-major, then m doubles of the original diagonal
+    double* gd = L + m * m;
+    __shared__ double inv_ljj;
+    for (int e = threadIdx.x; e < m * m; e += 256) L[e] = G[e];
+    for (int i = threadIdx.x; i < m; i += 256) gd[i] = G[(int64_t)i * m + i];
     __syncthreads();
     for (int j = 0; j < m; ++j) {
-        double part = 0.0;
-        for (int k = threadIdx.x; k < j; k += 256) part = fma(L[j * m + k], L[j * m + k], part);
-        const double sq = block_sum<256>(part, red);
-        const double gjj = G[(int64_t)j * m + j];
-        double d = gjj - sq;
-        if (!(d > tau * gjj) || !isfinite(d)) {
-            if (threadIdx.x == 0) { flags[j] = 1; atomicAdd(nbad, 1); }
-            d = (gjj > 0.0 && isfinite(gjj)) ? gjj : 1.0;
+        if (threadIdx.x == 0) {
+            double d = L[j * m + j];
+            const double gjj = gd[j];
+            if (!(d > tau * gjj) || !isfinite(d)) {
+                flags[j] = 1;
+                atomicAdd(nbad, 1);
+                d = (gjj > 0.0 && isfinite(gjj)) ? gjj : 1.0;
+            }
+            const double l = sqrt(d);
+            L[j * m + j] = l;
+            inv_ljj = 1.0 / l;
         }
-        const double ljj = sqrt(d);
-        if (threadIdx.x == 0) L[j * m + j] = ljj;
         __syncthreads();
-        for (int i = j + 1 + threadIdx.x; i < m; i += 256) {
-            double a = G[(int64_t)i * m + j];
-            for (int k = 0; k < j; ++k) a = fma(-L[i * m + k], L[j * m + k], a);
-            L[i * m + j] = a / ljj;
+        const double il = inv_ljj;
+        for (int i = j + 1 + threadIdx.x; i < m; i += 256) L[i * m + j] *= il;
+        __syncthreads();
+        const int t = m - j - 1;
+        for (int e = threadIdx.x; e < t * t; e += 256) {
+            const int i = j + 1 + e / t, k = j + 1 + e % t;
+            if (k <= i) L[i * m + k] = fma(-L[i * m + j], L[k * m + j], L[i * m + k]);
         }
         __syncthreads();
     }
-    for (int e = threadIdx.x; e < m * m; e += 256) Lout[e] = L[e];
+    for (int e = threadIdx.x; e < m * m; e += 256) Lout[e] = ((e % m) <= (e / m)) ? L[e] : 0.0;
 }
 
-// Q = Y L^{-T} row by row (forward substitution), in place allowed.
-__global__ void __launch_bounds__(128) k_trsm_rows(double* Y, const double* Lg, int64_t n, int m) {
-    extern __shared__ double L[];
+// Q = Y L^{-T} row by row (forward substitution), in place allowed; four
+// independent partial sums per dot product to hide FP64 latency.
+__global__ void __launch_bounds__(64) k_trsm_rows(double* Y, const double* Lg, int64_t n, int m) {
+    extern __shared__ double L[];   // m*m, then m inverse diagonals
+    double* dinv = L + m * m;
     for (int e = threadIdx.x; e < m * m; e += blockDim.x) L[e] = Lg[e];
+    for (int i = threadIdx.x; i < m; i += blockDim.x) dinv[i] = 1.0 / Lg[(int64_t)i * m + i];
     __syncthreads();
     const int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (r >= n) return;
     for (int j = 0; j < m; ++j) {
-        double a = Y[(int64_t)j * n + r];
-        for (int k = 0; k < j; ++k) a = fma(-L[j * m + k], Y[(int64_t)k * n + r], a);
-        Y[(int64_t)j * n + r] = a / L[j * m + j];
+        double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+        const double* lj = L + j * m;
+        int k = 0;
+        for (; k + 3 < j; k += 4) {
+            s0 = fma(lj[k], Y[(int64_t)k * n + r], s0);
+            s1 = fma(lj[k + 1], Y[(int64_t)(k + 1) * n + r], s1);
+            s2 = fma(lj[k + 2], Y[(int64_t)(k + 2) * n + r], s2);
+            s3 = fma(lj[k + 3], Y[(int64_t)(k + 3) * n + r], s3);
+        }
+        for (; k < j; ++k) s0 = fma(lj[k], Y[(int64_t)k * n + r], s0);
+        Y[(int64_t)j * n + r] = (Y[(int64_t)j * n + r] - ((s0 + s1) + (s2 + s3))) * dinv[j];
     }
 }
 
-// Cyclic Jacobi with parallel (round-robin) ordering on a symmetric m x m
-// matrix held in shared memory.  Rotation (p,q): tau = (h_qq - h_pp)/(2 h_pq),
-// t = sign(tau)/(|tau| + sqrt(1+tau^2)), c = 1/sqrt(1+t^2), s = t c;
-// H <- J^T H J, W <- W J.  Rotations with |h_pq| <= tol sqrt(|h_pp h_qq|) are
-// skipped; a sweep without rotations ends the iteration.  Output: theta
-// sorted descending and W (column-major) with columns in the same order.
-__global__ void __launch_bounds__(512) k_jacobi(const double* Hg, int m, double tol, int max_sweeps,
-                                                double* theta, double* Wout, int* status) {
-    extern __shared__ double sm[];
-    const int mp = m + (m & 1);            // even player count (dummy index m when odd)
-    double* H = sm;                        // m*m row-major
-    double* cs = H + m * m;                // 2 per pair
-    int* rot = (int*)(cs + mp);            // rotations this sweep
-    int* perm = rot + 1;                   // m
-    for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
-        const int i = e / m, j = e % m;
-        H[e] = 0.5 * (Hg[(int64_t)i * m + j] + Hg[(int64_t)j * m + i]);
-        Wout[(int64_t)j * m + i] = (i == j) ? 1.0 : 0.0;   // W column-major
+// Tall-skinny G = A^T B for column-major n x m blocks A, B: each CTA sums a
+// slab of rows into its own m x m partial (rows staged in shared memory);
+// k_gram_reduce adds the partials in slab order (deterministic).
+__global__ void __launch_bounds__(256) k_gram_partial(const double* A, const double* B, int64_t n, int m,
+                                                      int64_t rows_per_cta, double* part) {
+    extern __shared__ double sh[];   // rows_per_cta x m for A, then for B
+    const int64_t r0 = blockIdx.x * rows_per_cta;
+    const int64_t nr = max((int64_t)0, min(rows_per_cta, n - r0));
+    double* As = sh;
+    double* Bs = sh + rows_per_cta * m;
+    for (int64_t e = threadIdx.x; e < nr * m; e += 256) {
+        const int64_t c = e / nr, r = e % nr;
+        As[r * m + c] = A[c * n + r0 + r];
+        Bs[r * m + c] = B[c * n + r0 + r];
     }
     __syncthreads();
+    double* P = part + (int64_t)blockIdx.x * m * m;
+    for (int e = threadIdx.x; e < m * m; e += 256) {
+        const int i = e / m, j = e % m;
+        double s0 = 0.0, s1 = 0.0;
+        int64_t r = 0;
+        for (; r + 1 < nr; r += 2) {
+            s0 = fma(As[r * m + i], Bs[r * m + j], s0);
+            s1 = fma(As[(r + 1) * m + i], Bs[(r + 1) * m + j], s1);
+        }
+        if (r < nr) s0 = fma(As[r * m + i], Bs[r * m + j], s0);
+        P[e] = s0 + s1;
+    }
+}
+
+__global__ void k_gram_reduce(const double* part, int nparts, int m, double* G) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= m * m) return;
+    double s = 0.0;
+    for (int p = 0; p < nparts; ++p) s += part[(int64_t)p * m * m + e];
+    G[e] = s;
+}
+
+// Cyclic Jacobi sweeps with parallel (round-robin) ordering on a symmetric
+// m x m matrix H (row-major, shared memory), accumulating W <- W J (W
+// column-major).  Rotation (p,q): tau = (h_qq - h_pp)/(2 h_pq),
+// t = sign(tau)/(|tau| + sqrt(1+tau^2)), c = 1/sqrt(1+t^2), s = t c;
+// H <- J^T H J.  Rotations with |h_pq| <= tol sqrt(|h_pp h_qq|) are skipped
+// (relative-accuracy threshold for graded matrices); a sweep without
+// rotations ends the loop.  Returns the number of sweeps (max_sweeps + 1 if
+// the limit was hit).  All threads of the block call it.
+__device__ __forceinline__ void rr_pair(int r, int i, int mp, int& p, int& q) {
+    if (i == 0) { p = mp - 1; q = r; }
+    else { p = (r + i) % (mp - 1); q = (r - i + (mp - 1)) % (mp - 1); }
+    if (p > q) { const int x = p; p = q; q = x; }
+}
+
+template <typename T>
+__device__ int jacobi_sweeps(T* H, T* W, int m, T tol, int max_sweeps, T* cs, int* rot) {
+    const int mp = m + (m & 1);            // even player count (dummy index m when odd)
     const int npair = mp / 2;
-    int sweep = 0;
-    for (; sweep < max_sweeps; ++sweep) {
+    for (int sweep = 0; sweep < max_sweeps; ++sweep) {
         if (threadIdx.x == 0) *rot = 0;
         __syncthreads();
         for (int r = 0; r < mp - 1; ++r) {
             for (int i = threadIdx.x; i < npair; i += blockDim.x) {
                 int p, q;
-                if (i == 0) { p = mp - 1; q = r; }
-                else { p = (r + i) % (mp - 1); q = (r - i + (mp - 1)) % (mp - 1); }
-                if (p > q) { const int x = p; p = q; q = x; }
-                double c = 1.0, s = 0.0;
+                rr_pair(r, i, mp, p, q);
+                T c = 1, s = 0;
                 if (q < m) {
-                    const double hpq = H[p * m + q], hpp = H[p * m + p], hqq = H[q * m + q];
-                    if (fabs(hpq) > tol * sqrt(fabs(hpp * hqq)) && fabs(hpq) > 1e-300) {
-                        const double tau = (hqq - hpp) / (2.0 * hpq);
-                        const double t = (tau >= 0.0) ? 1.0 / (tau + sqrt(1.0 + tau * tau))
-                                                      : -1.0 / (-tau + sqrt(1.0 + tau * tau));
-                        c = 1.0 / sqrt(1.0 + t * t);
+                    const T hpq = H[p * m + q], hpp = H[p * m + p], hqq = H[q * m + q];
+                    if (fabs(hpq) > tol * sqrt(fabs(hpp * hqq)) && fabs(hpq) > (T)1e-300) {
+                        const T tau = (hqq - hpp) / (2 * hpq);
+                        const T t = (tau >= 0) ? 1 / (tau + sqrt(1 + tau * tau)) : -1 / (-tau + sqrt(1 + tau * tau));
+                        c = 1 / sqrt(1 + t * t);
                         s = t * c;
                         atomicAdd(rot, 1);
                     }
                 }
-                cs[2 * i] = c; cs[2 * i + 1] = s;
+                cs[2 * i] = c;
+                cs[2 * i + 1] = s;
             }
             __syncthreads();
             // columns: H <- H J, W <- W J
             for (int e = threadIdx.x; e < npair * m; e += blockDim.x) {
                 const int i = e / m, k = e % m;
-                const double s = cs[2 * i + 1];
-                if (s == 0.0) continue;
-                const double c = cs[2 * i];
+                const T s = cs[2 * i + 1];
+                if (s == 0) continue;
+                const T c = cs[2 * i];
                 int p, q;
-                if (i == 0) { p = mp - 1; q = r; }
-                else { p = (r + i) % (mp - 1); q = (r - i + (mp - 1)) % (mp - 1); }
-                if (p > q) { const int x = p; p = q; q = x; }
-                const double hkp = H[k * m + p], hkq = H[k * m + q];
+                rr_pair(r, i, mp, p, q);
+                const T hkp = H[k * m + p], hkq = H[k * m + q];
                 H[k * m + p] = c * hkp - s * hkq;
                 H[k * m + q] = s * hkp + c * hkq;
-                double* wp = Wout + (int64_t)p * m;
-                double* wq = Wout + (int64_t)q * m;
-                const double vp = wp[k], vq = wq[k];
+                T* wp = W + (int64_t)p * m;
+                T* wq = W + (int64_t)q * m;
+                const T vp = wp[k], vq = wq[k];
                 wp[k] = c * vp - s * vq;
                 wq[k] = s * vp + c * vq;
             }
@@ -202,36 +251,136 @@ __global__ void __launch_bounds__(512) k_jacobi(const double* Hg, int m, double 
             // rows: H <- J^T H
             for (int e = threadIdx.x; e < npair * m; e += blockDim.x) {
                 const int i = e / m, k = e % m;
-                const double s = cs[2 * i + 1];
-                if (s == 0.0) continue;
-                const double c = cs[2 * i];
+                const T s = cs[2 * i + 1];
+                if (s == 0) continue;
+                const T c = cs[2 * i];
                 int p, q;
-                if (i == 0) { p = mp - 1; q = r; }
-                else { p = (r + i) % (mp - 1); q = (r - i + (mp - 1)) % (mp - 1); }
-                if (p > q) { const int x = p; p = q; q = x; }
-                const double hpk = H[p * m + k], hqk = H[q * m + k];
+                rr_pair(r, i, mp, p, q);
+                const T hpk = H[p * m + k], hqk = H[q * m + k];
                 H[p * m + k] = c * hpk - s * hqk;
                 H[q * m + k] = s * hpk + c * hqk;
             }
             __syncthreads();
             for (int i = threadIdx.x; i < npair; i += blockDim.x) {
-                if (cs[2 * i + 1] == 0.0) continue;
+                if (cs[2 * i + 1] == 0) continue;
                 int p, q;
-                if (i == 0) { p = mp - 1; q = r; }
-                else { p = (r + i) % (mp - 1); q = (r - i + (mp - 1)) % (mp - 1); }
-                if (p > q) { const int x = p; p = q; q = x; }
-                H[p * m + q] = 0.0;
-                H[q * m + p] = 0.0;
+                rr_pair(r, i, mp, p, q);
+                H[p * m + q] = 0;
+                H[q * m + p] = 0;
             }
             __syncthreads();
         }
         const int nrot = *rot;
         __syncthreads();
-        if (nrot == 0) break;
+        if (nrot == 0) return sweep + 1;
     }
+    return max_sweeps + 1;
+}
+
+// Rayleigh-Ritz eigensolve of the symmetric m x m matrix Hg (global), in
+// two precisions:
+//  1. FP32 Jacobi on H / max|H| to a relative threshold of 1e-6 (the FP32
+//     pipe is ~60x the FP64 pipe on this part); rotations accumulate in W32;
+//  2. W = W32 in FP64, re-orthonormalised by Cholesky-QR (W^T W = L L^T,
+//     W <- W L^-T), and H' = W^T H W formed in FP64;
+//  3. FP64 Jacobi sweeps on H' (it starts ~1e-6 off diagonal, so two or three
+//     quadratically convergent sweeps finish it), W <- W J.
+// Output: theta sorted descending, W (column-major, global) in that order.
+// Shared memory: m*m doubles (H) + m*m doubles (two FP32 m*m arrays, later
+// the Gram/Cholesky matrix and the permutation scratch) + small arrays.
+__global__ void __launch_bounds__(512) k_jacobi(const double* Hg, int m, double tol, int max_sweeps,
+                                                double* theta, double* Wout, double* T1, int* status,
+                                                int* sweeps_out) {
+    extern __shared__ double sm[];
+    const int mp = m + (m & 1);
+    double* H = sm;                            // m*m
+    double* R2 = H + m * m;                    // m*m doubles of scratch
+    float* H32 = (float*)R2;                   // m*m floats
+    float* W32 = H32 + m * m;                  // m*m floats
+    double* cs64 = R2 + m * m;                 // mp
+    float* cs32 = (float*)(cs64 + mp);         // mp
+    int* rot = (int*)(cs32 + mp + (mp & 1));   // 1
+    int* perm = rot + 2;                       // m
+    __shared__ double hmax_s;
+    if (threadIdx.x == 0) hmax_s = 0.0;
+    __syncthreads();
+    double lmax = 0.0;
+    for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
+        const int i = e / m, j = e % m;
+        const double v = 0.5 * (Hg[(int64_t)i * m + j] + Hg[(int64_t)j * m + i]);
+        H[e] = v;
+        lmax = fmax(lmax, fabs(v));
+    }
+    for (int o = 16; o > 0; o >>= 1) lmax = fmax(lmax, __shfl_xor_sync(0xffffffffu, lmax, o));
+    if ((threadIdx.x & 31) == 0) atomicMax((unsigned long long*)&hmax_s, (unsigned long long)__double_as_longlong(lmax));
+    __syncthreads();
+    const double hscale = hmax_s > 0.0 ? 1.0 / hmax_s : 1.0;
+    for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
+        H32[e] = (float)(H[e] * hscale);
+        W32[e] = (e / m == e % m) ? 1.0f : 0.0f;
+    }
+    __syncthreads();
+    // 1. FP32 sweeps
+    const int s32 = jacobi_sweeps<float>(H32, W32, m, 1e-6f, 40, cs32, rot);
+    // 2. W (FP64) = W32, then Cholesky-QR of its columns
+    for (int e = threadIdx.x; e < m * m; e += blockDim.x) Wout[e] = (double)W32[e];
+    __syncthreads();
+    double* G = R2;   // the FP32 arrays are no longer needed
+    for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
+        const int i = e / m, j = e % m;
+        double a = 0.0;
+        for (int r = 0; r < m; ++r) a = fma(Wout[(int64_t)i * m + r], Wout[(int64_t)j * m + r], a);
+        G[e] = a;
+    }
+    __syncthreads();
+    for (int j = 0; j < m; ++j) {                  // left-looking Cholesky, in place (lower)
+        if (threadIdx.x == 0) {
+            double d = G[j * m + j];
+            for (int k = 0; k < j; ++k) d = fma(-G[j * m + k], G[j * m + k], d);
+            G[j * m + j] = sqrt(fmax(d, 1e-300));
+        }
+        __syncthreads();
+        const double ljj = G[j * m + j];
+        for (int i = j + 1 + threadIdx.x; i < m; i += blockDim.x) {
+            double a = G[i * m + j];
+            for (int k = 0; k < j; ++k) a = fma(-G[i * m + k], G[j * m + k], a);
+            G[i * m + j] = a / ljj;
+        }
+        __syncthreads();
+    }
+    for (int r = threadIdx.x; r < m; r += blockDim.x) {   // W <- W L^-T, row by row
+        for (int j = 0; j < m; ++j) {
+            double a = Wout[(int64_t)j * m + r];
+            for (int k = 0; k < j; ++k) a = fma(-G[j * m + k], Wout[(int64_t)k * m + r], a);
+            Wout[(int64_t)j * m + r] = a / G[j * m + j];
+        }
+    }
+    __syncthreads();
+    // H' = W^T H W  (T1 = H W in global scratch, then into H)
+    for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
+        const int r = e / m, j = e % m;
+        double a = 0.0;
+        for (int k = 0; k < m; ++k) a = fma(H[r * m + k], Wout[(int64_t)j * m + k], a);
+        T1[(int64_t)r * m + j] = a;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
+        const int i = e / m, j = e % m;
+        double a = 0.0;
+        for (int r = 0; r < m; ++r) a = fma(Wout[(int64_t)i * m + r], T1[(int64_t)r * m + j], a);
+        G[e] = a;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
+        const int i = e / m, j = e % m;
+        H[e] = 0.5 * (G[i * m + j] + G[j * m + i]);
+    }
+    __syncthreads();
+    // 3. FP64 sweeps
+    const int s64 = jacobi_sweeps<double>(H, Wout, m, tol, max_sweeps, cs64, rot);
     if (threadIdx.x == 0) {
-        if (sweep >= max_sweeps) atomicOr(status, ST_EIG_NOCONV);
-        // selection order, descending (stable for ties)
+        if (s64 > max_sweeps) atomicOr(status, ST_EIG_NOCONV);
+        if (sweeps_out) { atomicAdd(sweeps_out, s32); atomicAdd(sweeps_out + 1, s64); }
         for (int i = 0; i < m; ++i) perm[i] = i;
         for (int i = 0; i < m; ++i) {
             int best = i;
@@ -242,13 +391,12 @@ __global__ void __launch_bounds__(512) k_jacobi(const double* Hg, int m, double 
         for (int i = 0; i < m; ++i) theta[i] = H[perm[i] * m + perm[i]];
     }
     __syncthreads();
-    // permute W's columns into the sorted order (via H's storage, now free)
     for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
         const int col = e / m, row = e % m;
-        H[e] = Wout[(int64_t)perm[col] * m + row];
+        G[e] = Wout[(int64_t)perm[col] * m + row];
     }
     __syncthreads();
-    for (int e = threadIdx.x; e < m * m; e += blockDim.x) Wout[e] = H[e];
+    for (int e = threadIdx.x; e < m * m; e += blockDim.x) Wout[e] = G[e];
 }
 
 // max_i<dn |Z_i - theta_i QW_i| / theta_0, as bits of a non-negative double.
@@ -280,18 +428,33 @@ __global__ void k_to_isometry(const double* QW, int64_t n, int dn, double* U) {
 
 }  // namespace
 
+static size_t jacobi_smem(int m) {
+    const int mp = m + (m & 1);
+    return (size_t)2 * m * m * 8 + (size_t)mp * 8 + (size_t)(mp + 2) * 4 + (size_t)(m + 4) * 4 + 64;
+}
+
 static void set_smem(const void* fn, size_t bytes) {
     TRG_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
 }
 
 // Column-major n x m "A^T B" (m x m result, row-major) and "A W" products.
 static void gram(Ctx& ctx, const double* A, const double* B, int64_t n, int m, double* G, int precision) {
-    GemmDesc g;
-    g.M = m; g.N = m; g.K = n;
-    g.A.base = A; g.A.off_r = ctx.table({{m, n}}); g.A.off_c = ctx.table({{n, 1}}); g.A.c_fast = true;
-    g.B.base = B; g.B.off_r = ctx.table({{n, 1}}); g.B.off_c = ctx.table({{m, n}}); g.B.c_fast = false;
-    g.C = G; g.c_m = ctx.table({{m, m}}); g.c_n = ctx.table({{m, 1}}); g.beta = 0.0;
-    gemm(ctx, g, precision);
+    (void)precision;   // the Gram / Rayleigh-Ritz products are FP64 in every mode
+    const int64_t rows = std::max<int64_t>(8, (n + ctx.sm_count - 1) / ctx.sm_count);
+    const int64_t rows_c = std::min<int64_t>(rows, (int64_t)(96 * 1024 / (16 * m)));   // <= 96 KB staged
+    const int nparts = (int)((n + rows_c - 1) / rows_c);
+    ctx.ensure(ctx.f64_partial, (size_t)nparts * m * m * sizeof(double));
+    const size_t smem = (size_t)rows_c * m * 2 * sizeof(double);
+    static bool attr = false;
+    if (!attr) {
+        TRG_CUDA(cudaFuncSetAttribute((const void*)k_gram_partial, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      100 * 1024));
+        attr = true;
+    }
+    k_gram_partial<<<nparts, 256, smem, ctx.stream>>>(A, B, n, m, rows_c, ctx.f64_partial.as<double>());
+    TRG_LAUNCHED(ctx);
+    k_gram_reduce<<<(m * m + 255) / 256, 256, 0, ctx.stream>>>(ctx.f64_partial.as<double>(), nparts, m, G);
+    TRG_LAUNCHED(ctx);
 }
 static void times_small(Ctx& ctx, const double* A, const double* W, int64_t n, int m, double* C) {
     GemmDesc g;
@@ -313,18 +476,20 @@ static void orthonormalise(Ctx& ctx, double* Y, int64_t n, int m, double* G, dou
             k_col_normalize<<<m, 256, 0, ctx.stream>>>(Y, n, flags);
             TRG_LAUNCHED(ctx);
             gram(ctx, Y, Y, n, m, G, TRG_FP64);
-            k_chol_flag<<<1, 256, smem, ctx.stream>>>(G, L, m, pass == 0 ? 1e-8 : 1e-12, flags, nbad);
+            k_chol_flag<<<1, 256, smem + (size_t)m * 8, ctx.stream>>>(G, L, m, pass == 0 ? 1e-8 : 1e-12, flags,
+                                                                     nbad);
             TRG_LAUNCHED(ctx);
             int hb = 0;
             TRG_CUDA(cudaMemcpyAsync(&hb, nbad, sizeof(int), cudaMemcpyDeviceToHost, ctx.stream));
             TRG_CUDA(cudaStreamSynchronize(ctx.stream));
             if (hb == 0) break;
+            ctx.counters[4] += (uint64_t)hb;
             if (attempt >= 16) fail(TRG_ENUMERIC, "Cholesky-QR: could not complete a basis");
             dim3 grid((unsigned)std::min<int64_t>((n + 255) / 256, 64), (unsigned)m);
             k_rand_cols<<<grid, 256, 0, ctx.stream>>>(Y, n, m, flags, seed, ++salt);
             TRG_LAUNCHED(ctx);
         }
-        k_trsm_rows<<<(unsigned)((n + 31) / 32), 32, smem, ctx.stream>>>(Y, L, n, m);
+        k_trsm_rows<<<(unsigned)((n + 63) / 64), 64, smem + (size_t)m * 8, ctx.stream>>>(Y, L, n, m);
         TRG_LAUNCHED(ctx);
     }
 }
@@ -336,15 +501,15 @@ int isometry(Ctx& ctx, const double* M, int64_t n, int dcut, double* U, std::vec
     if (m > MAX_M) fail(TRG_ENOTSUP, "isometry: Dcut + oversampling exceeds the supported block (112)");
     static bool attrs = false;
     if (!attrs) {
-        set_smem((const void*)k_chol_flag, (size_t)MAX_M * MAX_M * 8);
-        set_smem((const void*)k_trsm_rows, (size_t)MAX_M * MAX_M * 8);
-        set_smem((const void*)k_jacobi, (size_t)MAX_M * MAX_M * 8 + (MAX_M + 2) * 8 + (MAX_M + 2) * 4);
+        set_smem((const void*)k_chol_flag, (size_t)MAX_M * MAX_M * 8 + MAX_M * 8);
+        set_smem((const void*)k_trsm_rows, (size_t)MAX_M * MAX_M * 8 + MAX_M * 8);
+        set_smem((const void*)k_jacobi, jacobi_smem(MAX_M));
         attrs = true;
     }
     // buffers: Q, Y, Z, QW (n x m each); G, L, W (m x m); theta (m)
     ctx.ensure(ctx.eig, (size_t)(4 * n * m) * sizeof(double));
     ctx.ensure(ctx.eig_small, (size_t)(3 * m * m + 2 * m + 8) * sizeof(double));
-    ctx.ensure(ctx.flags, (size_t)(m + 2) * sizeof(int));
+    ctx.ensure(ctx.flags, (size_t)(m + 8) * sizeof(int));
     double* Q = ctx.eig.as<double>();
     double* Y = Q + n * m;
     double* Z = Y + n * m;
@@ -355,6 +520,8 @@ int isometry(Ctx& ctx, const double* M, int64_t n, int dcut, double* U, std::vec
     double* theta = W + m * m;
     int* flags = ctx.flags.as<int>();
     int* nbad = flags + m;
+    int* sweeps = flags + m + 2;   // [0] FP32 sweeps, [1] FP64 sweeps of the last Rayleigh-Ritz
+
     int* status = ctx.status.as<int>();
     double* res_slot = ctx.scal.as<double>() + SC_RES;
     const uint64_t seed = ctx.cfg.seed ^ (0xA24BAED4963EE407ull * (uint64_t)step);
@@ -379,7 +546,7 @@ int isometry(Ctx& ctx, const double* M, int64_t n, int dcut, double* U, std::vec
         orthonormalise(ctx, Q, n, m, G, L, flags, nbad, seed, salt);
     }
 
-    const size_t jac_smem = (size_t)m * m * 8 + (m + 2) * 8 + (m + 2) * 4;
+    const size_t jac_smem = jacobi_smem(m);
     // Split products carry ~2^-(8S-1) relative error, which floors the Ritz
     // residual; f is insensitive to residuals far above that floor (1e-6
     // moves f by ~1e-12 on the Ising workloads), so stop at 2^-(8S-10).
@@ -397,7 +564,8 @@ int isometry(Ctx& ctx, const double* M, int64_t n, int dcut, double* U, std::vec
         gemm(ctx, g, precision);
         // Rayleigh-Ritz
         gram(ctx, Q, Y, n, m, G, TRG_FP64);
-        k_jacobi<<<1, 512, jac_smem, ctx.stream>>>(G, m, 1e-15, 60, theta, W, status);
+        TRG_CUDA(cudaMemsetAsync(sweeps, 0, 2 * sizeof(int), ctx.stream));
+        k_jacobi<<<1, 512, jac_smem, ctx.stream>>>(G, m, 1e-15, 60, theta, W, L, status, sweeps);
         TRG_LAUNCHED(ctx);
         times_small(ctx, Y, W, n, m, Z);
         times_small(ctx, Q, W, n, m, QW);
@@ -405,15 +573,26 @@ int isometry(Ctx& ctx, const double* M, int64_t n, int dcut, double* U, std::vec
         k_residual<<<dn_paper, 256, 0, ctx.stream>>>(Z, QW, theta, n, (unsigned long long*)res_slot);
         TRG_LAUNCHED(ctx);
         double res = 0.0;
+        int hsw[2] = {0, 0};
         TRG_CUDA(cudaMemcpyAsync(th.data(), theta, (size_t)m * sizeof(double), cudaMemcpyDeviceToHost, ctx.stream));
         TRG_CUDA(cudaMemcpyAsync(&res, res_slot, sizeof(double), cudaMemcpyDeviceToHost, ctx.stream));
+        TRG_CUDA(cudaMemcpyAsync(hsw, sweeps, 2 * sizeof(int), cudaMemcpyDeviceToHost, ctx.stream));
         TRG_CUDA(cudaStreamSynchronize(ctx.stream));
+        ctx.counters[0] += 1;
+        ctx.counters[1] += 1;
+        ctx.counters[2] += (uint64_t)hsw[0];
+        ctx.counters[3] += (uint64_t)hsw[1];
         if (read_status(ctx) & ST_EIG_NOCONV) fail(TRG_ENUMERIC, "Rayleigh-Ritz Jacobi did not converge");
         if (!(th[0] > 0.0) || !std::isfinite(th[0])) fail(TRG_ENUMERIC, "environment has no positive eigenvalue");
         if (res <= tol || m == n) {
             int dn = dn_paper;
             if (ctx.cfg.trunc == TRG_TRUNC_MULTIPLET && dn < n) {
-                while (dn > 1 && (th[(size_t)dn - 1] - th[(size_t)dn]) < ctx.cfg.gap_tol * th[0]) --dn;
+                // split products separate exactly degenerate eigenvalues by up
+                // to ~2^-(8S-12) lambda_1: treat smaller gaps as degenerate
+                double gtol = ctx.cfg.gap_tol;
+                if (precision == TRG_SPLIT_BF16)
+                    gtol = std::max(gtol, std::ldexp(1.0, -(8 * ctx.cfg.split_slices - 12)));
+                while (dn > 1 && (th[(size_t)dn - 1] - th[(size_t)dn]) < gtol * th[0]) --dn;
             }
             lam.assign(th.begin(), th.begin() + dn);
             const int64_t tot = n * dn;

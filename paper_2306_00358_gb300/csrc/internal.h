@@ -90,6 +90,9 @@ struct Ctx {
         std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pending;
     } ph[TRG_PHASE_COUNT];
     std::vector<cudaEvent_t> event_pool;
+    // diagnostics: subspace iterations, Rayleigh-Ritz solves, FP32 / FP64
+    // Jacobi sweeps, Cholesky-QR column repairs
+    uint64_t counters[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     cudaEvent_t get_event();
     // Record the start of a timed region of phase p (no-op unless profiling).
     int region_begin(int p);

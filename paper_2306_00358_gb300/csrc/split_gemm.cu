@@ -45,16 +45,18 @@ constexpr int BN = 128;
 constexpr int BK = 32;                        // K per stage: 64 bytes of BF16
 constexpr int TILE_BYTES = BM * BK * 2;       // 8 KB per 128 x 32 BF16 tile
 constexpr int CHUNK_STAGES = 1024 / BK;       // exact-accumulation run (1024 K)
-constexpr int EPI_WARPS = 8;
+constexpr int EPI_WARPS = 16;
 constexpr int THREADS = 64 + 32 * EPI_WARPS;  // TMA warp + MMA warp + epilogue
 constexpr uint32_t TMEM_COLS = 512;
 constexpr unsigned long long WAIT_NS = 2000000000ull;   // bounded mbarrier waits: 2 s
 
 __host__ __device__ constexpr int stages_for(int S) { return S <= 4 ? 3 : 2; }
+constexpr int CPT = 32;                        // accumulator columns per epilogue thread
+constexpr int STAGING_BYTES = EPI_WARPS * 32 * 8 * 8;    // epilogue store staging, 32 KB
 __host__ __device__ constexpr int smem_bytes_for(int S) {
     // at least 120 KB so that a second CTA (and its 512 TMEM columns) never shares the SM
-    return (stages_for(S) * 2 * S * TILE_BYTES + 1024 + 256) > 120 * 1024
-               ? stages_for(S) * 2 * S * TILE_BYTES + 1024 /*align*/ + 256 /*barriers*/
+    return (stages_for(S) * 2 * S * TILE_BYTES + 1024 + 256 + STAGING_BYTES) > 120 * 1024
+               ? stages_for(S) * 2 * S * TILE_BYTES + 1024 /*align*/ + 256 /*barriers*/ + STAGING_BYTES
                : 120 * 1024;
 }
 
@@ -147,6 +149,18 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
           "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
         : "r"(taddr));
 }
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&r)[8]) {
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                 : "r"(taddr));
+}
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
 // Exact int64 -> FP64 bits times 2^e2, round-to-nearest-even, integer
@@ -203,6 +217,7 @@ k_split_mma(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
     uint64_t* mma_done = acc_empty + 1;
     uint32_t* tmem_slot = (uint32_t*)(mma_done + 1);
     volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
+    double* staging = (double*)(smem + STAGES * STAGE_BYTES + 256);   // EPI_WARPS x 32 x 8 doubles
 
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
@@ -323,9 +338,9 @@ k_split_mma(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
         }
     } else {
         // ---------------------------------------------------------- epilogue
-        const int ew = warp - 2;                  // 0..7
+        const int ew = warp - 2;                  // 0..15
         const int quad = warp & 3;                // TMEM lane quadrant this warp may access
-        const int colh = ew >> 2;                 // which 64-column half
+        const int colh = ew >> 2;                 // which 32-column quarter
         const uint32_t lane_base = (uint32_t)(quad * 32) << 16;
         const int row_in_tile = quad * 32 + lane;
         const int nchunks = (num_kb + CHUNK_STAGES - 1) / CHUNK_STAGES;
@@ -333,9 +348,12 @@ k_split_mma(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
         bool ok = true;
         for (int tile = blockIdx.x; tile < num_tiles && ok; tile += gridDim.x) {
             const int mb = tile / tiles_n, nb = tile % tiles_n;
-            int i0[64], i1[64];
+            // J = I0 2^8 + I1: the exact ACC0 and ACC01 + ACC10 sums of this
+            // tile's columns in one int64 each; at the end J becomes
+            // V = J 2^14 + rint(ACCR 2^22) and then, in place, the FP64 bits
+            long long J[CPT];
 #pragma unroll
-            for (int j = 0; j < 64; ++j) { i0[j] = 0; i1[j] = 0; }
+            for (int j = 0; j < CPT; ++j) J[j] = 0;
             for (int c = 0; c < nchunks && ok; ++c) {
                 // one lane waits, the warp follows (the TMEM loads are warp-collective)
                 int w_ok = 1;
@@ -343,58 +361,77 @@ k_split_mma(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
                 ok = __shfl_sync(0xffffffffu, w_ok, 0) != 0;
                 if (!ok) break;
                 tc_fence_after();
+                const bool last = (c == nchunks - 1);
+                const int m = mb * BM + row_in_tile;
+                const bool row_ok = m < g.M;
+                const int ea = (last && row_ok) ? g.ea[m] : 0;
 #pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    const uint32_t col = (uint32_t)(colh * 64 + h * 32);
-                    uint32_t r[32];
-                    tmem_ld32(tmem + lane_base + col, r);
+                for (int h = 0; h < CPT / 8; ++h) {           // 8 columns at a time
+                    const uint32_t col = (uint32_t)(colh * CPT + h * 8);
+                    uint32_t r[8];
+                    tmem_ld8(tmem + lane_base + col, r);
                     tmem_wait_ld();
 #pragma unroll
-                    for (int j = 0; j < 32; ++j) i0[h * 32 + j] += __float2int_rn(__uint_as_float(r[j]));
-                    tmem_ld32(tmem + lane_base + 128 + col, r);
+                    for (int j = 0; j < 8; ++j) J[h * 8 + j] += (long long)__float2int_rn(__uint_as_float(r[j])) << 8;
+                    tmem_ld8(tmem + lane_base + 128 + col, r);
                     tmem_wait_ld();
 #pragma unroll
-                    for (int j = 0; j < 32; ++j) i1[h * 32 + j] += __float2int_rn(__uint_as_float(r[j]) * 256.0f);
-                    tmem_ld32(tmem + lane_base + 256 + col, r);
+                    for (int j = 0; j < 8; ++j) J[h * 8 + j] += __float2int_rn(__uint_as_float(r[j]) * 256.0f);
+                    tmem_ld8(tmem + lane_base + 256 + col, r);
                     tmem_wait_ld();
 #pragma unroll
-                    for (int j = 0; j < 32; ++j) i1[h * 32 + j] += __float2int_rn(__uint_as_float(r[j]) * 256.0f);
-                }
-                if (c == nchunks - 1) {
-                    // last chunk: fold in ACCR and write the tile's FP64 results
-                    const int m = mb * BM + row_in_tile;
-                    const bool row_ok = m < g.M;
-                    const int ea = row_ok ? g.ea[m] : 0;
-                    const int64_t cm = row_ok ? g.c_m[m] : 0;
-#pragma unroll
-                    for (int h = 0; h < 2; ++h) {
-                        const uint32_t col = (uint32_t)(colh * 64 + h * 32);
-                        uint32_t r[32];
+                    for (int j = 0; j < 8; ++j) J[h * 8 + j] += __float2int_rn(__uint_as_float(r[j]) * 256.0f);
+                    if (last) {
+                        // fold in ACCR and form these columns' FP64 results in place
                         if (S >= 3) {
-                            tmem_ld32(tmem + lane_base + 384 + col, r);
+                            tmem_ld8(tmem + lane_base + 384 + col, r);
                             tmem_wait_ld();
                         } else {
                             // two slices: no product lands in ACCR, whose columns are never written
 #pragma unroll
-                            for (int j = 0; j < 32; ++j) r[j] = 0u;
+                            for (int j = 0; j < 8; ++j) r[j] = 0u;
                         }
                         const int n0 = nb * BN + (int)col;
 #pragma unroll
-                        for (int j = 0; j < 32; ++j) {
+                        for (int j = 0; j < 8; ++j) {
                             const int n = n0 + j;
+                            double v = 0.0;
                             if (row_ok && n < g.N) {
-                                const long long v = ((long long)i0[h * 32 + j] << 22) +
-                                                    ((long long)i1[h * 32 + j] << 14) +
-                                                    __float2ll_rn(__uint_as_float(r[j]) * 4194304.0f);
-                                g.C[cm + g.c_n[n]] = scaled_i64_to_double(v, ea + g.eb[n] - 36);
+                                const long long iv = (J[h * 8 + j] << 14) +
+                                                     __float2ll_rn(__uint_as_float(r[j]) * 4194304.0f);
+                                v = scaled_i64_to_double(iv, ea + g.eb[n] - 36);
                             }
+                            J[h * 8 + j] = __double_as_longlong(v);
                         }
                     }
                 }
+                // TMEM is free for the next tile before the stores go out
                 tc_fence_before();
                 __syncwarp();
                 if (lane == 0) mbar_arrive(acc_empty);
                 ++chunk_no;
+                if (last) {
+                    // stores through the warp's 32 x 8 staging tile: lanes of a
+                    // quarter-warp then write 8 adjacent columns (64 B) of one row
+                    double* stg = staging + ew * (32 * 8);
+                    const int quarter = lane >> 3, cl = lane & 7;
+#pragma unroll
+                    for (int pass = 0; pass < CPT / 8; ++pass) {
+#pragma unroll
+                        for (int jj = 0; jj < 8; ++jj)
+                            stg[lane * 8 + (jj ^ ((lane >> 1) & 7))] = __longlong_as_double(J[pass * 8 + jj]);
+                        __syncwarp();
+                        const int n = nb * BN + colh * CPT + pass * 8 + cl;
+                        const int64_t cn = (n < g.N) ? g.c_n[n] : 0;
+#pragma unroll 4
+                        for (int q = 0; q < 8; ++q) {
+                            const int rr = 4 * q + quarter;
+                            const int mr = mb * BM + quad * 32 + rr;
+                            if (mr < g.M && n < g.N) g.C[g.c_m[mr] + cn] = stg[rr * 8 + (cl ^ ((rr >> 1) & 7))];
+                        }
+                        __syncwarp();
+                    }
+                }
             }
         }
     }

@@ -160,6 +160,13 @@ class Solver:
     def launch_count(self) -> int:
         return int(self._lib.trg_launch_count(self._h))
 
+    def counters(self) -> dict:
+        arr = (_lib.c_uint64 * 5)()
+        self._check(self._lib.trg_get_counters(self._h, arr, 5), "trg_get_counters")
+        names = ("subspace_iterations", "rayleigh_ritz", "jacobi_sweeps_fp32", "jacobi_sweeps_fp64",
+                 "cholqr_repairs")
+        return {k: int(v) for k, v in zip(names, arr)}
+
     def profile(self, on: bool = True):
         self._check(self._lib.trg_profile_enable(self._h, 1 if on else 0), "trg_profile_enable")
 

@@ -147,7 +147,7 @@ def test_identity_isometry_when_untruncated(monkeypatch):
     ref = hotrg.solve(t0, beta, 16, 6)
     real = hotrg.isometry
 
-    def identity_when_full(m, dcut, trunc="paper", gap_tol=1e-8):
+    def identity_when_full(m, dcut, trunc="paper", gap_tol=1e-6):
         n = m.shape[0]
         if min(n, dcut) == n:
             dx = int(round(math.sqrt(n)))
