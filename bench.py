@@ -49,6 +49,12 @@ def parse():
     ap.add_argument("--betas", default=None)
     ap.add_argument("--fields", default=None)
     ap.add_argument("--dcuts", default=None)
+    ap.add_argument("--batch", action="store_true", help="config 4: 128-instance coupling sweep")
+    ap.add_argument("--serve", action="store_true", help="config 5: Poisson stream of requests")
+    ap.add_argument("--requests", type=int, default=200)
+    ap.add_argument("--rate", type=float, default=2.0, help="serve: mean arrivals per second")
+    ap.add_argument("--slots", type=int, default=16)
+    ap.add_argument("--seed", type=int, default=1234)
     return ap.parse_args()
 
 
@@ -377,8 +383,100 @@ def run_sweep(args):
                       "max_abs_df_split_fp64": max(r["abs_df_split_fp64"] for r in out)}), flush=True)
 
 
+def _fp64_solve_seconds(dcut, nsteps=40, model="ising", beta=BETA_C, h=0.0):
+    """Time one plain FP64 solve on the GPU (the serial reference of the
+    batched and served runs)."""
+    import torch
+
+    from paper_2306_00358_gb300 import Solver
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    with Solver(0, precision="fp64", trunc="multiplet" if model == "xy" else "paper") as s:
+        s.init_tensor(model, beta, h)
+        s.coarse_grain(dcut, nsteps)
+        s.free_energy()
+    return time.perf_counter() - t0
+
+
+def run_batch(args):
+    """Batched coupling sweep: 128 independent Ising instances, beta on a
+    uniform grid in [0.38, 0.50] x h in {0, 1e-2}, Dcut drawn uniformly from
+    {16, 24, 32, 48} (seed 1234), 40 half-steps, split precision, run
+    concurrently through the solve engine; compared with serial plain FP64
+    solves (timed once per Dcut and summed over the drawn mix)."""
+    import numpy as np
+
+    from paper_2306_00358_gb300 import serving as sv
+    rng = np.random.default_rng(args.seed)
+    betas = np.linspace(0.38, 0.50, 64)
+    specs = []
+    for h in (0.0, 1e-2):
+        for b in betas:
+            specs.append(sv.Spec(model="ising", beta=float(b), h=h, dcut=int(rng.choice([16, 24, 32, 48])),
+                                 nsteps=40, precision="split", slices=args.slices))
+    t0 = time.perf_counter()
+    res = sv.batch_run(specs, slots=args.slots, hbm_budget_bytes=150 << 30, workspace_bytes=1 << 30)
+    wall = time.perf_counter() - t0
+    ok = sum(r["status"] == 0 for r in res)
+    counts = {d: sum(s.dcut == d for s in specs) for d in (16, 24, 32, 48)}
+    fp64 = {d: _fp64_solve_seconds(d) for d in (16, 24, 32, 48)}
+    serial = sum(counts[d] * fp64[d] for d in counts)
+    print(json.dumps({"mode": "batch", "workload": "128 Ising instances, beta grid [0.38,0.50] x h {0,1e-2}, "
+                      "Dcut U{16,24,32,48} (seed %d), 40 half-steps" % args.seed, "slots": args.slots,
+                      "solves": len(specs), "ok": ok, "wall_s": wall, "solves_per_s": len(specs) / wall,
+                      "serial_fp64_s_estimated": serial, "fp64_s_per_solve_by_dcut": fp64,
+                      "dcut_counts": counts, "speedup_vs_serial_fp64": serial / wall}), flush=True)
+
+
+def run_serve(args):
+    """Serving: a Poisson stream of requests (config 5 mix) into the solve
+    engine; reports p50/p99 latency and solves/s."""
+    import numpy as np
+
+    from paper_2306_00358_gb300 import serving as sv
+    rng = np.random.default_rng(args.seed)
+    dcuts = [16, 24, 32, 48, 64, 96]
+    weights = [0.30, 0.25, 0.20, 0.15, 0.07, 0.03]
+    specs = []
+    for _ in range(args.requests):
+        if rng.random() < 0.7:
+            model, beta = "ising", float(rng.uniform(0.35, 0.55))
+        else:
+            model, beta = "xy", float(rng.uniform(0.8, 1.3))
+        specs.append(sv.Spec(model=model, beta=beta, h=float(rng.choice([0.0, 1e-3, 1e-2])),
+                             dcut=int(rng.choice(dcuts, p=weights)), nsteps=int(rng.integers(20, 41)),
+                             precision="split", slices=args.slices,
+                             trunc="multiplet" if model == "xy" else "paper"))
+    gaps = rng.exponential(1.0 / args.rate, size=len(specs))
+    with sv.Server(0, slots=args.slots, hbm_budget_bytes=150 << 30, workspace_bytes=1 << 30) as s:
+        t0 = time.perf_counter()
+        tickets = []
+        for spec, gap in zip(specs, gaps):
+            time.sleep(gap)
+            tickets.append(s.submit(spec))
+        res = [s.wait(t) for t in tickets]
+        wall = time.perf_counter() - t0
+        st = s.stats()
+    lat = np.array([r["seconds_queued"] + r["seconds_run"] for r in res])
+    by_d = {}
+    for spec, r in zip(specs, res):
+        by_d.setdefault(spec.dcut, []).append(r["seconds_queued"] + r["seconds_run"])
+    print(json.dumps({"mode": "serve", "requests": len(specs), "rate_per_s": args.rate, "slots": args.slots,
+                      "ok": sum(r["status"] == 0 for r in res), "wall_s": wall,
+                      "p50_latency_s": float(np.percentile(lat, 50)), "p99_latency_s": float(np.percentile(lat, 99)),
+                      "solves_per_s": st["solves_per_s"], "peak_admitted_bytes": st["peak_bytes"],
+                      "p50_by_dcut": {d: float(np.percentile(v, 50)) for d, v in sorted(by_d.items())}}),
+          flush=True)
+
+
 def main():
     args = parse()
+    if args.batch:
+        run_batch(args)
+        return
+    if args.serve:
+        run_serve(args)
+        return
     if args.gemm:
         run_gemm(args)
         return

@@ -44,7 +44,9 @@ typedef enum trg_status {
     TRG_ENUMERIC = 4,  /* non-positive / NaN norm or trace, eigensolver not converged */
     TRG_ETIMEOUT = 5,  /* a bounded device-side wait ran out */
     TRG_ECUDA = 6,     /* a CUDA runtime call failed (see trg_last_error) */
-    TRG_ENOTSUP = 7    /* feature not available on this device / build */
+    TRG_ENOTSUP = 7,   /* feature not available on this device / build */
+    TRG_EAGAIN = 8,    /* serving: the request has not finished yet */
+    TRG_ECANCELED = 9  /* serving: the request was cancelled before it started */
 } trg_status;
 
 typedef enum trg_model { TRG_ISING = 0, TRG_XY = 1 } trg_model;
@@ -216,6 +218,85 @@ int trg_gemm(trg_ctx* ctx, int M, int N, int K, const double* A_dev, int lda, co
  */
 int trg_gemm_noalloc(int M, int N, int K, const double* A_dev, int lda, const double* B_dev, int ldb,
                      double* C_dev, int ldc, int slices, void* stream);
+
+/* ------------------------------------------------ batches and serving --- */
+/*
+ * Many independent free-energy solves on one GPU (the paper's runs are
+ * independent solves per coupling: Sec. 3.2 sweeps T and D, Sec. 3.3 sweeps
+ * T).  Each slot is a worker thread owning one context and one CUDA stream;
+ * a solve's tensors stay on the device until it finishes.  Requests queue
+ * FIFO and start when a slot is free and their estimated device memory
+ * (trg_solve_bytes) fits in what the HBM budget has left, so new requests
+ * are admitted while others run and their work overlaps on the device.
+ * Results do not depend on what else runs (same kernels, same arithmetic,
+ * no shared buffers).
+ */
+typedef struct trg_solve_spec {
+    int model;          /* TRG_ISING (D0 = 2) or TRG_XY (D0 odd) */
+    double beta, h;
+    int D0;
+    int Dcut;
+    int nsteps;         /* half-steps */
+    int precision;      /* TRG_FP64 or TRG_SPLIT_BF16 */
+    int split_slices;   /* 2..5 in TRG_SPLIT_BF16 */
+    int trunc;          /* trg_trunc */
+    uint64_t seed;      /* subspace-iteration start (0 = default) */
+} trg_solve_spec;
+
+typedef struct trg_solve_result {
+    int status;             /* trg_status of the solve */
+    double f;               /* free energy per site */
+    double lnz_per_site;
+    double seconds_queued;  /* submit -> start */
+    double seconds_run;     /* start -> finish */
+    int slot;               /* worker slot that ran it */
+} trg_solve_result;
+
+/* In dry-run mode a request with this seed reports TRG_ENUMERIC (host-side
+ * fault injection for tests of the scheduler; no effect on real solves). */
+#define TRG_DRY_RUN_FAIL_SEED 0xFA17FA17ull
+
+typedef struct trg_server_config {
+    int slots;                     /* concurrent solves (worker threads / streams), 1..256 */
+    size_t hbm_budget_bytes;       /* admission budget for the running solves' memory */
+    size_t workspace_bytes;        /* contraction workspace per solve (default 1 GiB) */
+    int dry_run;                   /* 1: no GPU work, slots sleep (tests of the scheduler) */
+    double dry_run_seconds_per_step;
+} trg_server_config;
+
+typedef struct trg_serve_stats {
+    uint64_t submitted, completed, failed, cancelled, running, queued;
+    size_t bytes_in_use, peak_bytes;     /* admitted estimates, now and at most */
+    double p50_latency_s, p99_latency_s, max_latency_s;   /* submit -> finish */
+    double solves_per_s;                 /* finished / (first submit .. last finish) */
+} trg_serve_stats;
+
+typedef struct trg_server trg_server;
+
+int trg_server_config_default(trg_server_config* cfg);
+int trg_solve_spec_default(trg_solve_spec* spec);
+/* Admission estimate (bytes) of one solve; workspace_bytes 0 = 1 GiB. */
+size_t trg_solve_bytes(const trg_solve_spec* spec, size_t workspace_bytes);
+
+int trg_serve_create(trg_server** out, int device, const trg_server_config* cfg);
+/* Queue a solve.  TRG_EINVAL for a bad spec, TRG_ENOMEM if its estimate
+ * exceeds the whole budget (it could never start). */
+int trg_serve_submit(trg_server* server, const trg_solve_spec* spec, uint64_t* ticket);
+/* TRG_OK and *out filled when done, TRG_EAGAIN while queued or running,
+ * TRG_ECANCELED after a cancel. */
+int trg_serve_poll(trg_server* server, uint64_t ticket, trg_solve_result* out);
+/* Block until done (timeout_s < 0: no limit); TRG_ETIMEOUT on expiry. */
+int trg_serve_wait(trg_server* server, uint64_t ticket, double timeout_s, trg_solve_result* out);
+/* Cancel a queued request (TRG_ESTATE if it already started). */
+int trg_serve_cancel(trg_server* server, uint64_t ticket);
+int trg_serve_get_stats(trg_server* server, trg_serve_stats* out);
+/* Stop: queued requests are dropped, running ones finish first. */
+int trg_serve_destroy(trg_server* server);
+
+/* Run n solves through a temporary server (cfg NULL = defaults); blocks.
+ * Returns the first failing status (each result carries its own). */
+int trg_batch_run(int device, const trg_solve_spec* specs, int n, const trg_server_config* cfg,
+                  trg_solve_result* results);
 
 /* ------------------------------------------------------- profiling ----- */
 /* Phases of a half-step, timed with CUDA events on the context's stream. */

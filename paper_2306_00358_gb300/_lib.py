@@ -47,6 +47,31 @@ class trg_phase_stats(ctypes.Structure):
 
 
 PHASES = ("env", "eig", "x1", "x2", "x3", "norm", "mma")
+TRG_EAGAIN, TRG_ECANCELED = 8, 9
+TRG_DRY_RUN_FAIL_SEED = 0xFA17FA17
+
+
+class trg_solve_spec(ctypes.Structure):
+    _fields_ = [("model", c_int), ("beta", c_double), ("h", c_double), ("D0", c_int), ("Dcut", c_int),
+                ("nsteps", c_int), ("precision", c_int), ("split_slices", c_int), ("trunc", c_int),
+                ("seed", c_uint64)]
+
+
+class trg_solve_result(ctypes.Structure):
+    _fields_ = [("status", c_int), ("f", c_double), ("lnz_per_site", c_double), ("seconds_queued", c_double),
+                ("seconds_run", c_double), ("slot", c_int)]
+
+
+class trg_server_config(ctypes.Structure):
+    _fields_ = [("slots", c_int), ("hbm_budget_bytes", c_size_t), ("workspace_bytes", c_size_t),
+                ("dry_run", c_int), ("dry_run_seconds_per_step", c_double)]
+
+
+class trg_serve_stats(ctypes.Structure):
+    _fields_ = [("submitted", c_uint64), ("completed", c_uint64), ("failed", c_uint64), ("cancelled", c_uint64),
+                ("running", c_uint64), ("queued", c_uint64), ("bytes_in_use", c_size_t), ("peak_bytes", c_size_t),
+                ("p50_latency_s", c_double), ("p99_latency_s", c_double), ("max_latency_s", c_double),
+                ("solves_per_s", c_double)]
 
 SIGNATURES = {
     "trg_config_default": (c_int, [ctypes.POINTER(trg_config)]),
@@ -70,6 +95,18 @@ SIGNATURES = {
                                  c_void_p]),
     "trg_profile_enable": (c_int, [c_void_p, c_int]),
     "trg_profile_read": (c_int, [c_void_p, c_int, ctypes.POINTER(trg_phase_stats)]),
+    "trg_server_config_default": (c_int, [ctypes.POINTER(trg_server_config)]),
+    "trg_solve_spec_default": (c_int, [ctypes.POINTER(trg_solve_spec)]),
+    "trg_solve_bytes": (c_size_t, [ctypes.POINTER(trg_solve_spec), c_size_t]),
+    "trg_serve_create": (c_int, [ctypes.POINTER(c_void_p), c_int, ctypes.POINTER(trg_server_config)]),
+    "trg_serve_submit": (c_int, [c_void_p, ctypes.POINTER(trg_solve_spec), ctypes.POINTER(c_uint64)]),
+    "trg_serve_poll": (c_int, [c_void_p, c_uint64, ctypes.POINTER(trg_solve_result)]),
+    "trg_serve_wait": (c_int, [c_void_p, c_uint64, c_double, ctypes.POINTER(trg_solve_result)]),
+    "trg_serve_cancel": (c_int, [c_void_p, c_uint64]),
+    "trg_serve_get_stats": (c_int, [c_void_p, ctypes.POINTER(trg_serve_stats)]),
+    "trg_serve_destroy": (c_int, [c_void_p]),
+    "trg_batch_run": (c_int, [c_int, ctypes.POINTER(trg_solve_spec), c_int, ctypes.POINTER(trg_server_config),
+                              ctypes.POINTER(trg_solve_result)]),
     "trg_status_string": (ctypes.c_char_p, [c_int]),
     "trg_last_error": (ctypes.c_char_p, [c_void_p]),
     "trg_launch_count": (c_uint64, [c_void_p]),

@@ -201,8 +201,6 @@ static void finish_init(Ctx& ctx, int Dx, int Dy, double beta) {
 using trg::Ctx;
 using trg::Error;
 
-struct trg_ctx : public Ctx {};
-
 #define TRG_GUARD_BEGIN try {
 #define TRG_GUARD_END(ctxp)                                                      \
     }                                                                            \
@@ -548,6 +546,8 @@ const char* trg_status_string(int status) {
         case TRG_ETIMEOUT: return "device wait timed out";
         case TRG_ECUDA: return "CUDA error";
         case TRG_ENOTSUP: return "not supported";
+        case TRG_EAGAIN: return "not finished yet";
+        case TRG_ECANCELED: return "cancelled";
         default: return "unknown status";
     }
 }

@@ -14,6 +14,7 @@
 // rounding, e.g. in the ordered phase).  All blocks are column-major (n x m).
 #include <algorithm>
 #include <cmath>
+#include <mutex>
 
 #include "internal.h"
 
@@ -445,12 +446,11 @@ static void gram(Ctx& ctx, const double* A, const double* B, int64_t n, int m, d
     const int nparts = (int)((n + rows_c - 1) / rows_c);
     ctx.ensure(ctx.f64_partial, (size_t)nparts * m * m * sizeof(double));
     const size_t smem = (size_t)rows_c * m * 2 * sizeof(double);
-    static bool attr = false;
-    if (!attr) {
+    static std::once_flag once;
+    std::call_once(once, [] {
         TRG_CUDA(cudaFuncSetAttribute((const void*)k_gram_partial, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       100 * 1024));
-        attr = true;
-    }
+    });
     k_gram_partial<<<nparts, 256, smem, ctx.stream>>>(A, B, n, m, rows_c, ctx.f64_partial.as<double>());
     TRG_LAUNCHED(ctx);
     k_gram_reduce<<<(m * m + 255) / 256, 256, 0, ctx.stream>>>(ctx.f64_partial.as<double>(), nparts, m, G);
@@ -499,13 +499,12 @@ int isometry(Ctx& ctx, const double* M, int64_t n, int dcut, double* U, std::vec
     const int dn_paper = (int)std::min<int64_t>(n, dcut);
     const int m = (int)std::min<int64_t>(n, (int64_t)dn_paper + std::max(1, ctx.cfg.oversample));
     if (m > MAX_M) fail(TRG_ENOTSUP, "isometry: Dcut + oversampling exceeds the supported block (112)");
-    static bool attrs = false;
-    if (!attrs) {
+    static std::once_flag once;
+    std::call_once(once, [] {
         set_smem((const void*)k_chol_flag, (size_t)MAX_M * MAX_M * 8 + MAX_M * 8);
         set_smem((const void*)k_trsm_rows, (size_t)MAX_M * MAX_M * 8 + MAX_M * 8);
         set_smem((const void*)k_jacobi, jacobi_smem(MAX_M));
-        attrs = true;
-    }
+    });
     // buffers: Q, Y, Z, QW (n x m each); G, L, W (m x m); theta (m)
     ctx.ensure(ctx.eig, (size_t)(4 * n * m) * sizeof(double));
     ctx.ensure(ctx.eig_small, (size_t)(3 * m * m + 2 * m + 8) * sizeof(double));

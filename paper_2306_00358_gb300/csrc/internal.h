@@ -160,5 +160,8 @@ void launch_fill(Ctx& ctx, double* x, int64_t n, double v);
 void launch_copy_strided(Ctx& ctx, const View4& src, const View4& dst);
 
 int read_status(Ctx& ctx);  // synchronises the stream
+void trim_buffers(Ctx& ctx);  // free every solve buffer (engine.cu)
 
 }  // namespace trg
+
+struct trg_ctx : public trg::Ctx {};

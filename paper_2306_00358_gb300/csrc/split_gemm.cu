@@ -533,13 +533,18 @@ __global__ void __launch_bounds__(256) k_slice(const double* __restrict__ src, c
 // ------------------------------------------------------------- host side ---
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
     static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-    if (!fn) {
+    static std::once_flag once;
+    static int err = 0;
+    std::call_once(once, [] {
         cudaDriverEntryPointQueryResult q;
         void* p = nullptr;
-        TRG_CUDA(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q));
-        if (q != cudaDriverEntryPointSuccess || !p) fail(TRG_ENOTSUP, "cuTensorMapEncodeTiled not available");
-        fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
-    }
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess || q != cudaDriverEntryPointSuccess || !p)
+            err = 1;
+        else
+            fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+    });
+    if (err || !fn) fail(TRG_ENOTSUP, "cuTensorMapEncodeTiled not available");
     return fn;
 }
 
@@ -559,11 +564,10 @@ CUtensorMap make_map(const void* base, int rows, int kp) {
 
 template <int S>
 void launch_mma(Ctx& ctx, const CUtensorMap& ta, const CUtensorMap& tb, const MmaArgs& a) {
-    static bool attr = false;
-    if (!attr) {
+    static std::once_flag once;
+    std::call_once(once, [] {
         TRG_CUDA(cudaFuncSetAttribute(k_split_mma<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes_for(S)));
-        attr = true;
-    }
+    });
     const int tiles = ((a.M + BM - 1) / BM) * ((a.N + BN - 1) / BN);
     const int grid = std::max(1, std::min(tiles, ctx.sm_count));
     k_split_mma<S><<<grid, THREADS, smem_bytes_for(S), ctx.stream>>>(ta, tb, a);
