@@ -42,7 +42,7 @@ def parse():
     ap.add_argument("--slices", type=int, default=4)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--solve", action="store_true", help="also time one full 40-half-step solve")
+    ap.add_argument("--no-solve", action="store_true", help="skip timing one full 40-half-step solve")
     ap.add_argument("--gemm", type=int, nargs=3, metavar=("M", "N", "K"), default=None,
                     help="micro-benchmark one split GEMM of this size instead of the half-step")
     ap.add_argument("--sweep", action="store_true", help="FP64 vs split solves over couplings (accuracy)")
@@ -267,7 +267,7 @@ def run_native(args):
         e2e = {"value": e2e_s, "unit": "s/half-step", "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": 16 + 8}
 
     solve = None
-    if args.solve:
+    if not args.no_solve:
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         s.init_tensor("ising", beta, 0.0)

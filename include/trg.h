@@ -49,7 +49,7 @@ typedef enum trg_status {
     TRG_ECANCELED = 9  /* serving: the request was cancelled before it started */
 } trg_status;
 
-typedef enum trg_model { TRG_ISING = 0, TRG_XY = 1 } trg_model;
+typedef enum trg_model { TRG_ISING = 0, TRG_XY = 1, TRG_POTTS = 2 } trg_model;
 
 /* Arithmetic of the contractions (environment, U.T.T.U, M.Q products).
  * Cholesky-QR, the Rayleigh-Ritz eigensolve, normalisation and the log-norm
@@ -115,6 +115,8 @@ int trg_set_precision(trg_ctx* ctx, int precision, int split_slices, int split_f
  *              (H = -sum s s' - h sum s).
  *   TRG_XY:    D0 odd (charges |n| <= (D0-1)/2);
  *              T = prod_legs sqrt(I_n(beta)) * I_{n_l+n_u-n_r-n_d}(beta h).
+ *   TRG_POTTS: D0 = q (2..8) states (Sec. 3.3): W_ss' = e^beta if s = s' else 1,
+ *              W = L L^T (Cholesky), T = sum_s e^{beta h [s=0]} L_si L_sj L_sk L_sl.
  * beta must be > 0 and finite, h finite.  T0 is divided by n0 = max|T0|.
  */
 int trg_init_tensor(trg_ctx* ctx, int model, double beta, double h, int D0);

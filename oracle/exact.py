@@ -141,6 +141,22 @@ def ising_lnz_exact(width: int, height: int, beta: float, h: float = 0.0) -> flo
     return emax + math.log(float(np.sum(np.exp(e - emax))))
 
 
+def potts_lnz_exact(width: int, height: int, beta: float, h: float = 0.0, q: int = 3) -> float:
+    """ln Z of the q-state Potts model on a torus by enumeration:
+    Z = sum_s exp(beta * #(equal neighbour pairs) + beta h * #(sites in state 0))."""
+    nsite = width * height
+    if q ** nsite > 5e7:
+        raise ValueError("lattice too large to enumerate")
+    states = np.arange(q ** nsite, dtype=np.int64)
+    digits = (states[:, None] // (q ** np.arange(nsite))) % q
+    s = digits.reshape(-1, height, width)
+    same = np.sum(s == np.roll(s, -1, axis=2), axis=(1, 2)) + np.sum(s == np.roll(s, -1, axis=1), axis=(1, 2))
+    zeros = np.sum(s == 0, axis=(1, 2))
+    e = beta * same + beta * h * zeros
+    emax = float(np.max(e))
+    return emax + math.log(float(np.sum(np.exp(e - emax))))
+
+
 def xy_lnz_exact(width: int, height: int, beta: float, h: float = 0.0, d0: int = 9) -> float:
     """ln Z of the charge-truncated XY model (|n| <= (d0-1)/2) on a torus, by
     summing over all bond charges of the character expansion:

@@ -90,6 +90,30 @@ def xy_tensor(beta: float, h: float = 0.0, d0: int = 9) -> np.ndarray:
     return t
 
 
+def potts_weight_factor(beta: float, q: int = 3) -> np.ndarray:
+    """Lower Cholesky factor L of the q-state Potts bond weight
+    W[s, s'] = e^beta if s == s' else 1 (Sec. 3.3), W = L L^T."""
+    w = np.ones((q, q)) + (math.exp(beta) - 1.0) * np.eye(q)
+    return np.linalg.cholesky(w)
+
+
+def potts_tensor(beta: float, h: float = 0.0, q: int = 3) -> np.ndarray:
+    """q-state Potts site tensor T[i,j,k,l] = sum_s e^{beta h [s=0]} L[s,i] L[s,j] L[s,k] L[s,l].
+
+    Sec. 3.3 prints T_ijkl = L_ia L_ib L_ic L_id, which drops the sum over the
+    spin index; contracting two such legs gives sum_i L[s,i] L[s',i] = W[s,s'],
+    so the network of T is Z.  The field h favours state 0 (the paper says a
+    field can be added to this tensor but does not give the form)."""
+    if not (beta >= 0.0 and math.isfinite(beta)):
+        raise ValueError("beta must be finite and >= 0")
+    L = potts_weight_factor(beta, q)
+    t = np.zeros((q, q, q, q))
+    for s in range(q):
+        ls = L[s]
+        t += math.exp(beta * h * (1.0 if s == 0 else 0.0)) * np.einsum("i,j,k,l->ijkl", ls, ls, ls, ls)
+    return t
+
+
 def initial_tensor(model: str, beta: float, h: float = 0.0, d0: int | None = None) -> np.ndarray:
     model = model.lower()
     if model == "ising":
@@ -98,4 +122,6 @@ def initial_tensor(model: str, beta: float, h: float = 0.0, d0: int | None = Non
         return ising_tensor(beta, h)
     if model == "xy":
         return xy_tensor(beta, h, 9 if d0 is None else d0)
+    if model == "potts":
+        return potts_tensor(beta, h, 3 if d0 is None else d0)
     raise ValueError(f"unknown model {model!r}")

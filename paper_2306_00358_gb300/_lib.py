@@ -18,7 +18,7 @@ P_double = ctypes.POINTER(ctypes.c_double)
 P_int = ctypes.POINTER(ctypes.c_int)
 
 TRG_OK, TRG_EINVAL, TRG_ESTATE, TRG_ENOMEM, TRG_ENUMERIC, TRG_ETIMEOUT, TRG_ECUDA, TRG_ENOTSUP = range(8)
-TRG_ISING, TRG_XY = 0, 1
+TRG_ISING, TRG_XY, TRG_POTTS = 0, 1, 2
 TRG_FP64, TRG_SPLIT_BF16 = 0, 1
 TRG_TRUNC_PAPER, TRG_TRUNC_MULTIPLET = 0, 1
 

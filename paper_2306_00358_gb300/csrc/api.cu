@@ -291,7 +291,7 @@ int trg_destroy(trg_ctx* ctx) {
     cudaStreamSynchronize(ctx->stream);
     Ctx& c = *ctx;
     for (trg::Buf* b : {&c.T, &c.Tnext, &c.M, &c.U, &c.scal, &c.status, &c.ws, &c.envP, &c.envQ, &c.eig,
-                        &c.eig_small, &c.flags, &c.split_ws, &c.f64_partial})
+                        &c.eig_small, &c.flags, &c.split_ws, &c.f64_partial, &c.cons_ef})
         c.release(*b);
     for (auto& kv : c.tables) c.release(kv.second);
     c.tables.clear();
@@ -356,6 +356,13 @@ int trg_init_tensor(trg_ctx* ctx, int model, double beta, double h, int D0) {
         const size_t n = (size_t)D0 * D0 * D0 * D0;
         ctx->ensure(ctx->T, n * sizeof(double));
         trg::launch_init_xy(*ctx, ctx->T.as<double>(), D0, beta, h);
+        trg::finish_init(*ctx, D0, D0, beta);
+    } else if (model == TRG_POTTS) {
+        if (D0 < 2 || D0 > 8) return bad(ctx, TRG_EINVAL, "Potts: D0 = q must be 2..8");
+        trg::reset_solve(*ctx);
+        const size_t n = (size_t)D0 * D0 * D0 * D0;
+        ctx->ensure(ctx->T, n * sizeof(double));
+        trg::launch_init_potts(*ctx, ctx->T.as<double>(), D0, beta, h);
         trg::finish_init(*ctx, D0, D0, beta);
     } else {
         return bad(ctx, TRG_EINVAL, "unknown model");

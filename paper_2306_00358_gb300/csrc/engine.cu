@@ -67,7 +67,7 @@ struct Request {
 };
 
 int validate_spec(const trg_solve_spec& s) {
-    if (s.model != TRG_ISING && s.model != TRG_XY) return TRG_EINVAL;
+    if (s.model != TRG_ISING && s.model != TRG_XY && s.model != TRG_POTTS) return TRG_EINVAL;
     if (!(s.beta > 0.0) || !std::isfinite(s.beta) || !std::isfinite(s.h)) return TRG_EINVAL;
     if (s.Dcut < 1 || s.nsteps < 0 || s.nsteps > 1000) return TRG_EINVAL;
     if (s.precision != TRG_FP64 && s.precision != TRG_SPLIT_BF16) return TRG_EINVAL;
@@ -75,6 +75,7 @@ int validate_spec(const trg_solve_spec& s) {
     if (s.trunc != TRG_TRUNC_PAPER && s.trunc != TRG_TRUNC_MULTIPLET) return TRG_EINVAL;
     if (s.model == TRG_ISING && s.D0 != 2) return TRG_EINVAL;
     if (s.model == TRG_XY && (s.D0 < 1 || s.D0 % 2 == 0 || s.D0 > 41)) return TRG_EINVAL;
+    if (s.model == TRG_POTTS && (s.D0 < 2 || s.D0 > 8)) return TRG_EINVAL;
     return TRG_OK;
 }
 
@@ -194,7 +195,7 @@ namespace trg {
 void trim_buffers(Ctx& c) {
     cudaStreamSynchronize(c.stream);
     for (Buf* b : {&c.T, &c.Tnext, &c.M, &c.U, &c.ws, &c.envP, &c.envQ, &c.eig, &c.eig_small, &c.flags,
-                   &c.split_ws, &c.f64_partial})
+                   &c.split_ws, &c.f64_partial, &c.cons_ef})
         c.release(*b);
     for (auto& kv : c.tables) c.release(kv.second);
     c.tables.clear();

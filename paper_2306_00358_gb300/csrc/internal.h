@@ -79,6 +79,7 @@ struct Ctx {
     Buf flags;             // per-column flags (int)
     Buf split_ws;          // split GEMM: exponents and BF16 slices of both operands
     Buf f64_partial;       // FP64 GEMM: split-K partial sums
+    Buf cons_ef;           // exponent fields recorded by a producing product (two halves)
     std::map<std::string, Buf> tables;  // cached offset tables
 
     // ---- phase timing
@@ -132,7 +133,16 @@ struct GemmDesc {
     double* C;
     const int64_t* c_m;
     const int64_t* c_n;
-    double beta;            // 0: overwrite, 1: accumulate
+    double beta = 0.0;      // 0: overwrite, 1: accumulate
+    // Split mode only.  Producer side: record, for the product that will
+    // consume C as its A operand, the largest FP64 exponent field of each of
+    // its rows (row of element (m, n) = cons_m[m] + cons_n[n]) into cons_ef
+    // (zeroed beforehand).  Consumer side: a_ef holds those fields for this
+    // product's A rows, so the exponent pass over A is skipped.
+    int* cons_ef = nullptr;
+    const int64_t* cons_m = nullptr;
+    const int64_t* cons_n = nullptr;
+    const int* a_ef = nullptr;
 };
 void gemm(Ctx& ctx, const GemmDesc& g, int precision);
 void gemm_f64(Ctx& ctx, const GemmDesc& g);
@@ -152,6 +162,7 @@ int isometry(Ctx& ctx, const double* M, int64_t n, int dcut, double* U, std::vec
 // Small kernels (small_kernels.cu)
 void launch_init_ising(Ctx& ctx, double* T, double beta, double h);
 void launch_init_xy(Ctx& ctx, double* T, int d0, double beta, double h);
+void launch_init_potts(Ctx& ctx, double* T, int q, double beta, double h);
 void launch_maxabs(Ctx& ctx, const double* x, int64_t n, double* slot_bits);
 void launch_normalise(Ctx& ctx, double* x, int64_t n, int step_weight_exp, bool initial);
 void launch_trace(Ctx& ctx, const double* T, int64_t Dx, int64_t Dy, double* slot);

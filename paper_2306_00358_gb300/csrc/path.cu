@@ -122,8 +122,11 @@ void environment(Ctx& ctx, const View4& t, double* M, int precision) {
 
 // Tx[i,j,k,l] = sum U[a,b,i] t[b,j,d,c] t[a,c,e,l] U[e,d,k], in slices of j:
 //   X1[(jj,i,d),(a,c)] = sum_b U[a,b,i] t[b,j0+jj,d,c]          (D^6)
-//   X2[(jj,i,d),(e,l)] = sum_{a,c} X1[(jj,i,d),(a,c)] t[a,c,e,l]  (D^7)
-//   O[i,j0+jj,k,l]     = sum_{d,e} X2[(jj,i,d),(e,l)] U[e,d,k]    (D^6)
+//   X2[(jj,i,l),(d,e)] = sum_{a,c} X1[(jj,i,d),(a,c)] t[a,c,e,l]  (D^7; columns of the
+//                        product ordered (l,e), stored so the next product reads (d,e) rows)
+//   O[i,j0+jj,k,l]     = sum_{d,e} X2[(jj,i,l),(d,e)] U[e,d,k]    (D^6)
+// In split mode each producer records the exponent fields of its consumer's
+// rows, so the consumer skips the exponent pass over the D^5 slice.
 void contract(Ctx& ctx, const View4& t, const double* U, int64_t Dn, const View4& out, int precision) {
     const int64_t Dx = t.n[0], Dy = t.n[1];
     const int64_t* s = t.s;
@@ -135,6 +138,15 @@ void contract(Ctx& ctx, const View4& t, const double* U, int64_t Dn, const View4
     ctx.ensure(ctx.ws, per_j * (size_t)jb);
     double* X1 = ctx.ws.as<double>();
     double* X2 = X1 + jb * Dn * Dx * DD;
+    const bool split = precision == TRG_SPLIT_BF16;
+    const int64_t rows2 = jb * Dn * Dx, rows3 = jb * Dn * Dy;   // A rows of the two consumers
+    int* ef2 = nullptr;
+    int* ef3 = nullptr;
+    if (split) {
+        ctx.ensure(ctx.cons_ef, (size_t)(rows2 + rows3) * sizeof(int));
+        ef2 = ctx.cons_ef.as<int>();
+        ef3 = ef2 + rows2;
+    }
 
     for (int64_t j0 = 0; j0 < Dy; j0 += jb) {
         const int64_t jn = std::min(jb, Dy - j0);
@@ -147,7 +159,13 @@ void contract(Ctx& ctx, const View4& t, const double* U, int64_t Dn, const View4
             g.C = X1;
             g.c_m = ctx.table({{Dx, Dy}, {Dn, Dx * DD}});
             g.c_n = ctx.table({{jb, Dn * Dx * DD}, {Dx, DD}, {Dy, 1}});
-            g.beta = 0.0;
+            if (split) {
+                // consumer row of element ((a,i),(jj,d,c)) is (jj,i,d)
+                TRG_CUDA(cudaMemsetAsync(ef2, 0, (size_t)rows2 * sizeof(int), ctx.stream));
+                g.cons_ef = ef2;
+                g.cons_m = ctx.table({{Dx, 0}, {Dn, Dx}});
+                g.cons_n = ctx.table({{jb, Dn * Dx}, {Dx, 1}, {Dy, 0}});
+            }
             gemm(ctx, g, precision);
         }
         {   // X2 (the D^7 product)
@@ -155,23 +173,30 @@ void contract(Ctx& ctx, const View4& t, const double* U, int64_t Dn, const View4
             GemmDesc g;
             g.M = jn * Dn * Dx; g.N = DD; g.K = DD;
             g.A = gather(ctx, X1, {{jb * Dn * Dx, DD}}, {{DD, 1}});
-            g.B = gather(ctx, t.p, {{Dx, s[0]}, {Dy, s[1]}}, {{Dx, s[2]}, {Dy, s[3]}});
+            g.B = gather(ctx, t.p, {{Dx, s[0]}, {Dy, s[1]}}, {{Dy, s[3]}, {Dx, s[2]}});
             g.C = X2;
-            g.c_m = ctx.table({{jb * Dn * Dx, DD}});
-            g.c_n = ctx.table({{DD, 1}});
-            g.beta = 0.0;
+            g.c_m = ctx.table({{jb * Dn, Dy * Dx * Dx}, {Dx, Dx}});
+            g.c_n = ctx.table({{Dy, Dx * Dx}, {Dx, 1}});
+            if (split) {
+                g.a_ef = ef2;
+                // consumer row of element ((jj,i,d),(l,e)) is (jj,i,l)
+                TRG_CUDA(cudaMemsetAsync(ef3, 0, (size_t)rows3 * sizeof(int), ctx.stream));
+                g.cons_ef = ef3;
+                g.cons_m = ctx.table({{jb * Dn, Dy}, {Dx, 0}});
+                g.cons_n = ctx.table({{Dy, 1}, {Dx, 0}});
+            }
             gemm(ctx, g, precision);
         }
         {   // O
             ctx.phase = TRG_PHASE_X3;
             GemmDesc g;
             g.M = jn * Dn * Dy; g.N = Dn; g.K = Dx * Dx;
-            g.A = gather(ctx, X2, {{jb, Dn * Dx * DD}, {Dn, Dx * DD}, {Dy, 1}}, {{Dx, DD}, {Dx, Dy}});
+            g.A = gather(ctx, X2, {{jb * Dn * Dy, Dx * Dx}}, {{Dx * Dx, 1}});
             g.B = gather(ctx, U, {{Dx, Dn}, {Dx, Dx * Dn}}, {{Dn, 1}});
             g.C = out.p + j0 * o[1];
             g.c_m = ctx.table({{jb, o[1]}, {Dn, o[0]}, {Dy, o[3]}});
             g.c_n = ctx.table({{Dn, o[2]}});
-            g.beta = 0.0;
+            if (split) g.a_ef = ef3;
             gemm(ctx, g, precision);
         }
     }

@@ -59,6 +59,32 @@ __global__ void k_init_xy(double* T, int d0, double beta, double h) {
     T[e] = legs * bessel_i_series(nl + nu - nr - nd, beta * h);
 }
 
+// q-state Potts (q <= 8): W = L L^T with W_ss' = e^beta (s = s'), 1 otherwise;
+// T[i,j,k,l] = sum_s e^{beta h [s=0]} L[s,i] L[s,j] L[s,k] L[s,l].
+// Each thread factors the small W itself (plain Cholesky, row by row).
+__global__ void k_init_potts(double* T, int q, double beta, double h) {
+    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t tot = (int64_t)q * q * q * q;
+    if (e >= tot) return;
+    double L[8][8];
+    const double eb = exp(beta);
+    for (int i = 0; i < q; ++i) {
+        for (int j = 0; j <= i; ++j) {
+            double a = (i == j) ? eb : 1.0;
+            for (int k = 0; k < j; ++k) a -= L[i][k] * L[j][k];
+            L[i][j] = (i == j) ? sqrt(a) : a / L[j][j];
+        }
+        for (int j = i + 1; j < q; ++j) L[i][j] = 0.0;
+    }
+    const int l = (int)(e % q), k = (int)((e / q) % q), j = (int)((e / q / q) % q), i = (int)(e / q / q / q);
+    double t = 0.0;
+    for (int s = 0; s < q; ++s) {
+        const double w = (s == 0) ? exp(beta * h) : 1.0;
+        t += w * L[s][i] * L[s][j] * L[s][k] * L[s][l];
+    }
+    T[e] = t;
+}
+
 __global__ void __launch_bounds__(256) k_maxabs(const double* __restrict__ x, int64_t n,
                                                 unsigned long long* out_bits) {
     double mx = 0.0;
@@ -170,6 +196,12 @@ void launch_init_ising(Ctx& ctx, double* T, double beta, double h) {
 void launch_init_xy(Ctx& ctx, double* T, int d0, double beta, double h) {
     const int64_t tot = (int64_t)d0 * d0 * d0 * d0;
     k_init_xy<<<(unsigned)((tot + 127) / 128), 128, 0, ctx.stream>>>(T, d0, beta, h);
+    TRG_LAUNCHED(ctx);
+}
+
+void launch_init_potts(Ctx& ctx, double* T, int q, double beta, double h) {
+    const int64_t tot = (int64_t)q * q * q * q;
+    k_init_potts<<<(unsigned)((tot + 127) / 128), 128, 0, ctx.stream>>>(T, q, beta, h);
     TRG_LAUNCHED(ctx);
 }
 

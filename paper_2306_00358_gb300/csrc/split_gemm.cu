@@ -201,6 +201,9 @@ struct MmaArgs {
     const int64_t* c_m;
     const int64_t* c_n;
     int* status;
+    int* cons_ef;              // optional: exponent fields of the consumer's rows
+    const int64_t* cons_m;
+    const int64_t* cons_n;
 };
 
 template <int S>
@@ -404,6 +407,29 @@ k_split_mma(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
                             J[h * 8 + j] = __double_as_longlong(v);
                         }
                     }
+                }
+                if (last && g.cons_ef && row_ok) {
+                    // exponent fields of the consumer's rows: run-length maxima
+                    // over this thread's columns, one atomic per run
+                    const int64_t cm0 = g.cons_m[m];
+                    int64_t cur = -1;
+                    int cur_max = 0;
+#pragma unroll
+                    for (int j = 0; j < CPT; ++j) {
+                        const int n = nb * BN + colh * CPT + j;
+                        if (n < g.N) {
+                            const int64_t crow = cm0 + g.cons_n[n];
+                            const int ef = (int)(((unsigned long long)J[j] >> 52) & 0x7FF);
+                            if (crow != cur) {
+                                if (cur >= 0 && cur_max) atomicMax(&g.cons_ef[cur], cur_max);
+                                cur = crow;
+                                cur_max = ef;
+                            } else {
+                                cur_max = max(cur_max, ef);
+                            }
+                        }
+                    }
+                    if (cur >= 0 && cur_max) atomicMax(&g.cons_ef[cur], cur_max);
                 }
                 // TMEM is free for the next tile before the stores go out
                 tc_fence_before();
@@ -634,7 +660,14 @@ void gemm_split(Ctx& ctx, const GemmDesc& d) {
     Gather bt2 = bt;
     bt2.c_fast = false;
     // contiguous along k in memory?  (the k-table of B is B.off_r)
-    row_exponents(ctx, d.A, M, K, ea);
+    if (d.a_ef) {
+        // the producing product already recorded A's exponent fields
+        TRG_CUDA(cudaMemcpyAsync(ea, d.a_ef, (size_t)M * sizeof(int), cudaMemcpyDeviceToDevice, ctx.stream));
+        k_exponent_finish<<<(unsigned)((M + 255) / 256), 256, 0, ctx.stream>>>(ea, M);
+        TRG_LAUNCHED(ctx);
+    } else {
+        row_exponents(ctx, d.A, M, K, ea);
+    }
     row_exponents(ctx, bt2, N, K, eb);
     switch (S) {
         case 2: launch_slice<2>(ctx, d.A, M, K, Mp, Kp, ea, sa); launch_slice<2>(ctx, bt2, N, K, Np, Kp, eb, sb); break;
@@ -649,6 +682,7 @@ void gemm_split(Ctx& ctx, const GemmDesc& d) {
     a.M = M; a.N = N; a.Kp = Kp; a.Mp = Mp; a.Np = Np; a.S = S;
     a.ea = ea; a.eb = eb; a.C = d.C; a.c_m = d.c_m; a.c_n = d.c_n;
     a.status = ctx.status.as<int>();
+    a.cons_ef = d.cons_ef; a.cons_m = d.cons_m; a.cons_n = d.cons_n;
     const int tok = ctx.region_begin(TRG_PHASE_MMA);
     switch (S) {
         case 2: launch_mma<2>(ctx, ta, tb, a); break;
@@ -790,6 +824,7 @@ extern "C" int trg_gemm_noalloc(int M, int N, int K, const double* A, int lda, c
         MmaArgs a;
         a.M = M; a.N = N; a.Kp = Kp; a.Mp = Mp; a.Np = Np; a.S = S;
         a.ea = ea; a.eb = eb; a.C = C; a.c_m = cm; a.c_n = cn; a.status = status;
+        a.cons_ef = nullptr; a.cons_m = nullptr; a.cons_n = nullptr;
         const int tiles = ((M + BM - 1) / BM) * ((N + BN - 1) / BN);
         const int grid = std::max(1, std::min(tiles, sms));
         switch (S) {

@@ -10,7 +10,7 @@ from dataclasses import dataclass
 from . import _lib
 from ._lib import check
 
-_MODELS = {"ising": _lib.TRG_ISING, "xy": _lib.TRG_XY}
+_MODELS = {"ising": _lib.TRG_ISING, "xy": _lib.TRG_XY, "potts": _lib.TRG_POTTS}
 _PREC = {"fp64": _lib.TRG_FP64, "split": _lib.TRG_SPLIT_BF16}
 _TRUNC = {"paper": _lib.TRG_TRUNC_PAPER, "multiplet": _lib.TRG_TRUNC_MULTIPLET}
 
@@ -30,7 +30,7 @@ class Spec:
 
     def c(self) -> _lib.trg_solve_spec:
         m = _MODELS[self.model]
-        d0 = self.d0 if self.d0 is not None else (2 if m == _lib.TRG_ISING else 9)
+        d0 = self.d0 if self.d0 is not None else {_lib.TRG_ISING: 2, _lib.TRG_XY: 9, _lib.TRG_POTTS: 3}[m]
         return _lib.trg_solve_spec(m, float(self.beta), float(self.h), int(d0), int(self.dcut), int(self.nsteps),
                                    _PREC[self.precision], int(self.slices), _TRUNC[self.trunc], int(self.seed))
 

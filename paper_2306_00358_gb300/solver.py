@@ -13,7 +13,7 @@ import numpy as np
 from . import _lib
 from ._lib import TRGError, check  # noqa: F401  (re-exported)
 
-_MODELS = {"ising": _lib.TRG_ISING, "xy": _lib.TRG_XY}
+_MODELS = {"ising": _lib.TRG_ISING, "xy": _lib.TRG_XY, "potts": _lib.TRG_POTTS}
 _PREC = {"fp64": _lib.TRG_FP64, "split": _lib.TRG_SPLIT_BF16, "split_bf16": _lib.TRG_SPLIT_BF16}
 _TRUNC = {"paper": _lib.TRG_TRUNC_PAPER, "multiplet": _lib.TRG_TRUNC_MULTIPLET}
 
@@ -115,7 +115,7 @@ class Solver:
     def init_tensor(self, model: str, beta: float, h: float = 0.0, d0: int | None = None):
         m = _MODELS[model.lower()]
         if d0 is None:
-            d0 = 2 if m == _lib.TRG_ISING else 9
+            d0 = {_lib.TRG_ISING: 2, _lib.TRG_XY: 9, _lib.TRG_POTTS: 3}[m]
         self._check(self._lib.trg_init_tensor(self._h, m, float(beta), float(h), int(d0)), "trg_init_tensor")
 
     def init_tensor_raw(self, t: np.ndarray, beta: float):

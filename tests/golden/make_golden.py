@@ -22,6 +22,7 @@ CASES = [
     ("ising_b0.48_d10_n21", "ising", 0.48, 0.0, 10, 21, "paper"),
     ("xy_b1.0_d12_n12", "xy", 1.0, 0.0, 12, 12, "multiplet"),
     ("xy_b1.1_d20_h0.05_n8", "xy", 1.1, 0.05, 20, 8, "multiplet"),
+    ("potts_bc_d12_n30", "potts", math.log(1 + math.sqrt(3)), 0.0, 12, 30, "multiplet"),
 ]
 
 
@@ -60,6 +61,12 @@ def main():
             ex[f"ising_b{beta}_h{h}_n{nsteps}"] = {"model": "ising", "beta": beta, "h": h, "nsteps": nsteps,
                                                    "width": w, "height": hh,
                                                    "lnz": exact.ising_lnz_exact(w, hh, beta, h)}
+    for (beta, h) in [(1.0, 0.0), (0.8, 0.05)]:
+        for nsteps in (2, 3):
+            w, hh = exact.hotrg_block(nsteps)
+            ex[f"potts_b{beta}_h{h}_n{nsteps}"] = {"model": "potts", "beta": beta, "h": h, "nsteps": nsteps,
+                                                   "width": w, "height": hh,
+                                                   "lnz": exact.potts_lnz_exact(w, hh, beta, h, 3)}
     for (beta, h) in [(1.0, 0.0), (0.9, 0.1)]:
         for nsteps in (1, 2):
             w, hh = exact.hotrg_block(nsteps)

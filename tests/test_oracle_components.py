@@ -158,3 +158,29 @@ def test_xy_enumeration_known_cases():
     s = sum(models.bessel_i(n, beta) for n in range(-4, 5))
     ref = math.log(s * s * models.bessel_i(0, beta * h))
     assert exact.xy_lnz_exact(1, 1, beta, h) == pytest.approx(ref, abs=1e-13)
+
+
+# ------------------------------------------------------------------ Potts ---
+def test_potts_cholesky_reconstructs_bond_weight():
+    for beta in (0.3, math.log(1 + math.sqrt(3)), 2.0):
+        L = models.potts_weight_factor(beta, 3)
+        w = np.ones((3, 3)) + (math.exp(beta) - 1.0) * np.eye(3)
+        assert np.abs(L @ L.T - w).max() <= 1e-14 * w.max()
+        assert np.allclose(np.triu(L, 1), 0.0)
+
+
+def test_potts_single_site_trace():
+    # one site closed on itself: two self-bonds, each W_ss = e^beta
+    beta, h = 0.7, 0.3
+    t = models.potts_tensor(beta, h, 3)
+    ref = sum(math.exp(2 * beta + beta * h * (s == 0)) for s in range(3))
+    assert hotrg.trace_pbc(t) == pytest.approx(ref, rel=1e-14)
+
+
+def test_potts_enumeration_known_cases():
+    # beta = 0: Z = q^V
+    assert exact.potts_lnz_exact(2, 2, 0.0) == pytest.approx(4 * math.log(3), abs=1e-13)
+    # q = 2 Potts with W = e^{beta delta} is Ising at K = beta/2 (+ beta per bond pair)
+    beta = 0.9
+    ref = exact.ising_lnz_exact(2, 2, beta / 2) + 8 * beta / 2
+    assert exact.potts_lnz_exact(2, 2, beta, q=2) == pytest.approx(ref, abs=1e-12)

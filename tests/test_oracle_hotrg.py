@@ -158,3 +158,21 @@ def test_identity_isometry_when_untruncated(monkeypatch):
     monkeypatch.setattr(hotrg, "isometry", identity_when_full)
     ident = hotrg.solve(t0, beta, 16, 6)
     assert abs(ident.f - ref.f) <= 1e-13
+
+
+@pytest.mark.parametrize("nsteps", [2, 3])
+@pytest.mark.parametrize("beta,h", [(1.0, 0.0), (0.8, 0.05)])
+def test_potts_untruncated_matches_enumeration(nsteps, beta, h):
+    width, height = exact.hotrg_block(nsteps)
+    sol = hotrg.solve(models.potts_tensor(beta, h, 3), beta, NO_TRUNC, nsteps)
+    lnz = sol.lnz_per_site * width * height
+    ref = exact.potts_lnz_exact(width, height, beta, h, 3)
+    assert abs(lnz - ref) <= 1e-12 * max(1.0, abs(ref))
+
+
+def test_potts_q2_is_ising_onsager():
+    # q = 2 Potts with W = e^{beta delta} equals Ising at K = beta/2, plus beta per site
+    beta = 0.6
+    sol = hotrg.solve(models.potts_tensor(beta, 0.0, 2), beta, 16, 40)
+    ref = exact.onsager_integral(beta / 2) + beta
+    assert abs(sol.lnz_per_site - ref) <= 1e-9
