@@ -128,28 +128,40 @@ __global__ void __launch_bounds__(256) k_chol_flag(const double* G, double* Lout
     for (int e = threadIdx.x; e < m * m; e += 256) Lout[e] = ((e % m) <= (e / m)) ? L[e] : 0.0;
 }
 
-// Q = Y L^{-T} row by row (forward substitution), in place allowed; four
-// independent partial sums per dot product to hide FP64 latency.
-__global__ void __launch_bounds__(64) k_trsm_rows(double* Y, const double* Lg, int64_t n, int m) {
-    extern __shared__ double L[];   // m*m, then m inverse diagonals
+// Q = Y L^{-T} row by row (forward substitution), in place allowed.  Each
+// thread keeps its row in shared memory (FP64 latency, not throughput, bounds
+// a dependent chain through global memory); four partial sums per dot.
+constexpr int TRSM_THREADS = 32;
+__global__ void __launch_bounds__(TRSM_THREADS) k_trsm_rows(double* Y, const double* Lg, int64_t n, int m) {
+    extern __shared__ double L[];   // m*m, then m inverse diagonals, then TRSM_THREADS rows of m
     double* dinv = L + m * m;
+    double* rows = dinv + m;
     for (int e = threadIdx.x; e < m * m; e += blockDim.x) L[e] = Lg[e];
     for (int i = threadIdx.x; i < m; i += blockDim.x) dinv[i] = 1.0 / Lg[(int64_t)i * m + i];
+    const int64_t r0 = (int64_t)blockIdx.x * TRSM_THREADS;
+    for (int e = threadIdx.x; e < m * TRSM_THREADS; e += blockDim.x) {
+        const int j = e / TRSM_THREADS, t = e % TRSM_THREADS;
+        rows[t * (m + 1) + j] = (r0 + t < n) ? Y[(int64_t)j * n + r0 + t] : 0.0;
+    }
     __syncthreads();
-    const int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (r >= n) return;
+    double* x = rows + threadIdx.x * (m + 1);
     for (int j = 0; j < m; ++j) {
         double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
         const double* lj = L + j * m;
         int k = 0;
         for (; k + 3 < j; k += 4) {
-            s0 = fma(lj[k], Y[(int64_t)k * n + r], s0);
-            s1 = fma(lj[k + 1], Y[(int64_t)(k + 1) * n + r], s1);
-            s2 = fma(lj[k + 2], Y[(int64_t)(k + 2) * n + r], s2);
-            s3 = fma(lj[k + 3], Y[(int64_t)(k + 3) * n + r], s3);
+            s0 = fma(lj[k], x[k], s0);
+            s1 = fma(lj[k + 1], x[k + 1], s1);
+            s2 = fma(lj[k + 2], x[k + 2], s2);
+            s3 = fma(lj[k + 3], x[k + 3], s3);
         }
-        for (; k < j; ++k) s0 = fma(lj[k], Y[(int64_t)k * n + r], s0);
-        Y[(int64_t)j * n + r] = (Y[(int64_t)j * n + r] - ((s0 + s1) + (s2 + s3))) * dinv[j];
+        for (; k < j; ++k) s0 = fma(lj[k], x[k], s0);
+        x[j] = (x[j] - ((s0 + s1) + (s2 + s3))) * dinv[j];
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < m * TRSM_THREADS; e += blockDim.x) {
+        const int j = e / TRSM_THREADS, t = e % TRSM_THREADS;
+        if (r0 + t < n) Y[(int64_t)j * n + r0 + t] = rows[t * (m + 1) + j];
     }
 }
 
@@ -291,7 +303,7 @@ __device__ int jacobi_sweeps(T* H, T* W, int m, T tol, int max_sweeps, T* cs, in
 // the Gram/Cholesky matrix and the permutation scratch) + small arrays.
 __global__ void __launch_bounds__(512) k_jacobi(const double* Hg, int m, double tol, int max_sweeps,
                                                 double* theta, double* Wout, double* T1, int* status,
-                                                int* sweeps_out) {
+                                                int* sweeps_out, int fp64_sweeps) {
     extern __shared__ double sm[];
     const int mp = m + (m & 1);
     double* H = sm;                            // m*m
@@ -377,8 +389,9 @@ __global__ void __launch_bounds__(512) k_jacobi(const double* Hg, int m, double 
         H[e] = 0.5 * (G[i * m + j] + G[j * m + i]);
     }
     __syncthreads();
-    // 3. FP64 sweeps
-    const int s64 = jacobi_sweeps<double>(H, Wout, m, tol, max_sweeps, cs64, rot);
+    // 3. FP64 sweeps (skipped for a rough Rayleigh-Ritz far from convergence:
+    //    then theta is the diagonal of H' and W the re-orthonormalised W32)
+    const int s64 = fp64_sweeps ? jacobi_sweeps<double>(H, Wout, m, tol, max_sweeps, cs64, rot) : 0;
     if (threadIdx.x == 0) {
         if (s64 > max_sweeps) atomicOr(status, ST_EIG_NOCONV);
         if (sweeps_out) { atomicAdd(sweeps_out, s32); atomicAdd(sweeps_out + 1, s64); }
@@ -489,7 +502,8 @@ static void orthonormalise(Ctx& ctx, double* Y, int64_t n, int m, double* G, dou
             k_rand_cols<<<grid, 256, 0, ctx.stream>>>(Y, n, m, flags, seed, ++salt);
             TRG_LAUNCHED(ctx);
         }
-        k_trsm_rows<<<(unsigned)((n + 63) / 64), 64, smem + (size_t)m * 8, ctx.stream>>>(Y, L, n, m);
+        k_trsm_rows<<<(unsigned)((n + TRSM_THREADS - 1) / TRSM_THREADS), TRSM_THREADS,
+                      smem + (size_t)m * 8 + (size_t)TRSM_THREADS * (m + 1) * 8, ctx.stream>>>(Y, L, n, m);
         TRG_LAUNCHED(ctx);
     }
 }
@@ -502,7 +516,7 @@ int isometry(Ctx& ctx, const double* M, int64_t n, int dcut, double* U, std::vec
     static std::once_flag once;
     std::call_once(once, [] {
         set_smem((const void*)k_chol_flag, (size_t)MAX_M * MAX_M * 8 + MAX_M * 8);
-        set_smem((const void*)k_trsm_rows, (size_t)MAX_M * MAX_M * 8 + MAX_M * 8);
+        set_smem((const void*)k_trsm_rows, (size_t)MAX_M * MAX_M * 8 + MAX_M * 8 + TRSM_THREADS * (MAX_M + 1) * 8);
         set_smem((const void*)k_jacobi, jacobi_smem(MAX_M));
     });
     // buffers: Q, Y, Z, QW (n x m each); G, L, W (m x m); theta (m)
@@ -531,16 +545,20 @@ int isometry(Ctx& ctx, const double* M, int64_t n, int dcut, double* U, std::vec
         k_rand_cols<<<grid, 256, 0, ctx.stream>>>(Q, n, m, nullptr, seed, salt);
         TRG_LAUNCHED(ctx);
     }
-    orthonormalise(ctx, Q, n, m, G, L, flags, nbad, seed, salt);
-    // two plain block power steps before the first Rayleigh-Ritz: the random
-    // start is mostly noise, and the Jacobi solve of a dense H is the costly part
-    for (int pre = 0; pre < 2 && m < n; ++pre) {
+    // Y = M Q
+    auto apply_m = [&]() {
         GemmDesc g;
         g.M = n; g.N = m; g.K = n;
         g.A.base = M; g.A.off_r = ctx.table({{n, n}}); g.A.off_c = ctx.table({{n, 1}}); g.A.c_fast = true;
         g.B.base = Q; g.B.off_r = ctx.table({{n, 1}}); g.B.off_c = ctx.table({{m, n}}); g.B.c_fast = false;
         g.C = Y; g.c_m = ctx.table({{n, 1}}); g.c_n = ctx.table({{m, n}}); g.beta = 0.0;
         gemm(ctx, g, precision);
+    };
+    orthonormalise(ctx, Q, n, m, G, L, flags, nbad, seed, salt);
+    // two plain block power steps before the first Rayleigh-Ritz: the random
+    // start is mostly noise, and the Jacobi solve of a dense H is the costly part
+    for (int pre = 0; pre < 2 && m < n; ++pre) {
+        apply_m();
         std::swap(Q, Y);
         orthonormalise(ctx, Q, n, m, G, L, flags, nbad, seed, salt);
     }
@@ -553,18 +571,32 @@ int isometry(Ctx& ctx, const double* M, int64_t n, int dcut, double* U, std::vec
     if (precision == TRG_SPLIT_BF16) tol = std::max(tol, std::ldexp(1.0, -(8 * ctx.cfg.split_slices - 10)));
     std::vector<double> th((size_t)m);
     const int max_it = std::max(1, ctx.cfg.eig_max_iter);
+    // Rayleigh-Ritz is the costly part (a one-SM Jacobi solve), so it is not
+    // done after every product: the first one, in FP32 only, measures the
+    // residual and the convergence rate rho ~ theta_m / theta_dn; the power
+    // steps needed to reach the tolerance follow from rho and run without a
+    // Rayleigh-Ritz; the next (full FP64) one normally converges.
+    int pending = 0;                 // planned plain power steps
+    int rr_done = 0;
+    double prev_res = 0.0;
+    int since_rr = 0;                // products applied since the previous Rayleigh-Ritz
     for (int it = 1; it <= max_it; ++it) {
+        if (pending > 0) {
+            apply_m();
+            std::swap(Q, Y);
+            orthonormalise(ctx, Q, n, m, G, L, flags, nbad, seed, salt);
+            --pending;
+            ++since_rr;
+            ctx.counters[0] += 1;
+            continue;
+        }
         // Y = M Q
-        GemmDesc g;
-        g.M = n; g.N = m; g.K = n;
-        g.A.base = M; g.A.off_r = ctx.table({{n, n}}); g.A.off_c = ctx.table({{n, 1}}); g.A.c_fast = true;
-        g.B.base = Q; g.B.off_r = ctx.table({{n, 1}}); g.B.off_c = ctx.table({{m, n}}); g.B.c_fast = false;
-        g.C = Y; g.c_m = ctx.table({{n, 1}}); g.c_n = ctx.table({{m, n}}); g.beta = 0.0;
-        gemm(ctx, g, precision);
+        apply_m();
         // Rayleigh-Ritz
         gram(ctx, Q, Y, n, m, G, TRG_FP64);
         TRG_CUDA(cudaMemsetAsync(sweeps, 0, 2 * sizeof(int), ctx.stream));
-        k_jacobi<<<1, 512, jac_smem, ctx.stream>>>(G, m, 1e-15, 60, theta, W, L, status, sweeps);
+        const int full = (rr_done > 0 || m == n) ? 1 : 0;
+        k_jacobi<<<1, 512, jac_smem, ctx.stream>>>(G, m, 1e-15, 60, theta, W, L, status, sweeps, full);
         TRG_LAUNCHED(ctx);
         times_small(ctx, Y, W, n, m, Z);
         times_small(ctx, Q, W, n, m, QW);
@@ -583,7 +615,7 @@ int isometry(Ctx& ctx, const double* M, int64_t n, int dcut, double* U, std::vec
         ctx.counters[3] += (uint64_t)hsw[1];
         if (read_status(ctx) & ST_EIG_NOCONV) fail(TRG_ENUMERIC, "Rayleigh-Ritz Jacobi did not converge");
         if (!(th[0] > 0.0) || !std::isfinite(th[0])) fail(TRG_ENUMERIC, "environment has no positive eigenvalue");
-        if (res <= tol || m == n) {
+        if ((res <= tol && full) || m == n) {
             int dn = dn_paper;
             if (ctx.cfg.trunc == TRG_TRUNC_MULTIPLET && dn < n) {
                 // split products separate exactly degenerate eigenvalues by up
@@ -599,6 +631,16 @@ int isometry(Ctx& ctx, const double* M, int64_t n, int dcut, double* U, std::vec
             TRG_LAUNCHED(ctx);
             return dn;
         }
+        // plan the power steps to the next Rayleigh-Ritz
+        double rho = th[(size_t)m - 1] / th[(size_t)dn_paper - 1];
+        if (rr_done > 0 && prev_res > 0.0 && res > 0.0 && since_rr > 0)
+            rho = std::max(rho, std::pow(res / prev_res, 1.0 / since_rr));
+        rho = std::min(std::max(rho, 0.05), 0.98);
+        int k = (res > tol) ? (int)std::ceil(std::log(tol / res) / std::log(rho)) : 0;
+        pending = std::min(std::max(k, 0), 40);   // k - 1 needed after the product below, plus one spare
+        ++rr_done;
+        prev_res = res;
+        since_rr = 1;
         // next block: orth(Y W) = orth(M Q W), same span as M Q
         std::swap(Q, Z);
         orthonormalise(ctx, Q, n, m, G, L, flags, nbad, seed, salt);
