@@ -40,6 +40,8 @@ def parse():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--precision", default=None, choices=["split", "fp64"])
     ap.add_argument("--slices", type=int, default=4)
+    ap.add_argument("--mma-pairs", type=int, default=0, choices=[0, 1],
+                    help="split products on CTA pairs (1) or one CTA per tile (0)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-solve", action="store_true", help="skip timing one full 40-half-step solve")
@@ -195,7 +197,7 @@ def run_native(args):
         torch.cuda.synchronize()
 
     stream = torch.cuda.current_stream()
-    s = Solver(local, stream=stream, precision=precision, split_slices=args.slices)
+    s = Solver(local, stream=stream, precision=precision, split_slices=args.slices, mma_pairs=args.mma_pairs)
     # replicas: every rank solves its own coupling (beta_c shifted per rank)
     beta = BETA_C * (1.0 + 1e-4 * rank)
     s.init_tensor("ising", beta, 0.0)
@@ -309,7 +311,7 @@ def run_gemm(args):
     rng = np.random.default_rng(3)
     a = torch.from_numpy(rng.standard_normal((m, k))).cuda()
     b = torch.from_numpy(rng.standard_normal((k, n))).cuda()
-    s = Solver(0, precision=precision, split_slices=args.slices)
+    s = Solver(0, precision=precision, split_slices=args.slices, mma_pairs=args.mma_pairs)
     for _ in range(max(1, args.warmup)):
         s.gemm(a, b)
     s.profile(True)
@@ -322,7 +324,7 @@ def run_gemm(args):
     ph = s.phase_stats()
     mma = ph["mma"]
     line = {"mode": "gemm", "m": m, "n": n, "k": k, "precision": precision, "slices": args.slices,
-            "seconds_per_gemm": wall, "fp64_equiv_tflops": 2.0 * m * n * k / wall / 1e12}
+            "mma_pairs": args.mma_pairs, "seconds_per_gemm": wall, "fp64_equiv_tflops": 2.0 * m * n * k / wall / 1e12}
     if mma["calls"]:
         t = mma["ms"] / mma["calls"] / 1e3
         line.update({"mma_ms": t * 1e3, "mma_tflops": mma["mma_flops"] / mma["calls"] / t / 1e12})

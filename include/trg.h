@@ -78,6 +78,10 @@ typedef struct trg_config {
     int eig_max_iter;        /* subspace iterations before TRG_ENUMERIC (default 300) */
     uint64_t seed;           /* seed of the start block of the subspace iteration */
     size_t workspace_bytes;  /* bound on the contraction workspace (0 = 4 GiB) */
+    int mma_pairs;           /* TRG_SPLIT_BF16: 1 runs products with more than 128 rows on
+                                CTA pairs (256-row tiles, cta_group::2, each CTA staging
+                                half of B); 0 (default) keeps one CTA per 128 x 128 tile.
+                                Results are identical either way. */
 } trg_config;
 
 typedef struct trg_ctx trg_ctx;

@@ -39,6 +39,7 @@ class trg_config(ctypes.Structure):
         ("eig_max_iter", c_int),
         ("seed", c_uint64),
         ("workspace_bytes", c_size_t),
+        ("mma_pairs", c_int),
     ]
 
 

@@ -237,6 +237,7 @@ int trg_config_default(trg_config* cfg) {
     cfg->eig_max_iter = 300;
     cfg->seed = 0x5EEDull;
     cfg->workspace_bytes = 0;
+    cfg->mma_pairs = 0;
     return TRG_OK;
 }
 
@@ -244,6 +245,7 @@ static int validate_config(const trg_config& c) {
     if (c.precision != TRG_FP64 && c.precision != TRG_SPLIT_BF16) return TRG_EINVAL;
     if (c.split_slices < 2 || c.split_slices > 5) return TRG_EINVAL;
     if (c.split_from_step < 0) return TRG_EINVAL;
+    if (c.mma_pairs != 0 && c.mma_pairs != 1) return TRG_EINVAL;
     if (c.trunc != TRG_TRUNC_PAPER && c.trunc != TRG_TRUNC_MULTIPLET) return TRG_EINVAL;
     if (!(c.gap_tol >= 0.0) || !(c.eig_tol > 0.0) || c.oversample < 1 || c.eig_max_iter < 1) return TRG_EINVAL;
     return TRG_OK;

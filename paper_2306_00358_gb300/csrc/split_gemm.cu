@@ -24,9 +24,21 @@
 // Kernel layout: persistent, one CTA per SM, 128 x 128 output tiles, BF16
 // operand tiles of 128 x 32 staged by TMA (64-byte swizzle) through an
 // mbarrier pipeline; warp 0 issues TMA, warp 1 owns TMEM and issues
-// tcgen05.mma (one thread), warps 2..9 drain TMEM (two warps per 32-lane
-// quadrant, 64 columns each).  Every wait is bounded: on expiry the kernel
-// records ST_TIMEOUT and leaves its loops.
+// tcgen05.mma (one thread), 16 epilogue warps drain TMEM (four per 32-lane
+// quadrant, 32 columns each).  Per 16-wide K step the exact products are one
+// N = 256 MMA (A0 against the adjacent B0|B1 tiles, into the adjacent ACC0|
+// ACC01 columns) and one N = 128 MMA (A1 B0); the remainder products are
+// issued while the epilogue drains a finished 1024-K chunk, so the tensor
+// pipe keeps working across the drain.  Waiting threads are suspended in
+// mbarrier.try_wait rather than spinning (spinning costs shared-memory
+// cycles that the MMA operand reads need).  Every wait is bounded: on
+// expiry the kernel records ST_TIMEOUT and leaves its loops.
+//
+// A second instance runs each 256 x 128 tile on a CTA pair (cta_group::2):
+// each CTA stages its own 128 rows of A and half of B, the even CTA issues
+// the MMAs for both, and its barriers collect the loads and TMEM drains of
+// the pair.  It gives identical results; on this part it measured about 4 %
+// slower than the single-CTA kernel, so it is off by default (mma_pairs).
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
@@ -50,15 +62,30 @@ constexpr int THREADS = 64 + 32 * EPI_WARPS;  // TMA warp + MMA warp + epilogue
 constexpr uint32_t TMEM_COLS = 512;
 constexpr unsigned long long WAIT_NS = 2000000000ull;   // bounded mbarrier waits: 2 s
 
-__host__ __device__ constexpr int stages_for(int S) { return S <= 4 ? 3 : 2; }
 constexpr int CPT = 32;                        // accumulator columns per epilogue thread
 constexpr int STAGING_BYTES = EPI_WARPS * 32 * 8 * 8;    // epilogue store staging, 32 KB
-__host__ __device__ constexpr int smem_bytes_for(int S) {
+constexpr int SMEM_LIMIT = 232448;             // opt-in shared memory per block
+
+// CG = CTAs per MMA (1, or a pair with cta_group::2).  A CTA stages its own
+// 128 rows of A and 128 / CG columns of B per slice and stage.
+__host__ __device__ constexpr int b_tile_bytes(int CG) { return TILE_BYTES / CG; }
+__host__ __device__ constexpr int stage_bytes_for(int S, int CG) { return S * (TILE_BYTES + b_tile_bytes(CG)); }
+__host__ __device__ constexpr int stages_for(int S, int CG) {
+    return CG == 1 ? (S <= 4 ? 3 : 2)
+                   : ((SMEM_LIMIT - 1024 - 256 - STAGING_BYTES) / stage_bytes_for(S, CG) > 6
+                          ? 6
+                          : (SMEM_LIMIT - 1024 - 256 - STAGING_BYTES) / stage_bytes_for(S, CG));
+}
+__host__ __device__ constexpr int smem_bytes_for(int S, int CG) {
     // at least 120 KB so that a second CTA (and its 512 TMEM columns) never shares the SM
-    return (stages_for(S) * 2 * S * TILE_BYTES + 1024 + 256 + STAGING_BYTES) > 120 * 1024
-               ? stages_for(S) * 2 * S * TILE_BYTES + 1024 /*align*/ + 256 /*barriers*/ + STAGING_BYTES
+    return (stages_for(S, CG) * stage_bytes_for(S, CG) + 1024 + 256 + STAGING_BYTES) > 120 * 1024
+               ? stages_for(S, CG) * stage_bytes_for(S, CG) + 1024 /*align*/ + 256 /*barriers*/ + STAGING_BYTES
                : 120 * 1024;
 }
+static_assert(smem_bytes_for(2, 2) <= SMEM_LIMIT && smem_bytes_for(3, 2) <= SMEM_LIMIT &&
+                  smem_bytes_for(4, 2) <= SMEM_LIMIT && smem_bytes_for(5, 2) <= SMEM_LIMIT &&
+                  smem_bytes_for(5, 1) <= SMEM_LIMIT,
+              "split MMA shared memory");
 
 // ------------------------------------------------------------ PTX helpers
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -88,16 +115,27 @@ __device__ __forceinline__ unsigned long long global_ns() {
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
     return t;
 }
+// As mbar_try, but the thread is suspended until the phase completes or
+// about `hint_ns` pass, instead of spinning on shared memory (a spinning
+// waiter takes shared-memory cycles that the MMA operand reads need).
+__device__ __forceinline__ bool mbar_try_suspend(uint64_t* bar, uint32_t parity, uint32_t hint_ns) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity), "r"(hint_ns)
+        : "memory");
+    return ok != 0;
+}
 // Bounded wait; returns false (and flags the status word) on expiry or when
 // another role of the CTA has already given up.
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag,
                                           int* status) {
     if (mbar_try(bar, parity)) return true;
     const unsigned long long t0 = global_ns();
-    unsigned n = 0;
-    while (!mbar_try(bar, parity)) {
+    while (!mbar_try_suspend(bar, parity, 2000u)) {
         if (*abort_flag) return false;
-        if ((++n & 255u) == 0 && global_ns() - t0 > WAIT_NS) {
+        if (global_ns() - t0 > WAIT_NS) {
             *abort_flag = 1;
             atomicOr(status, ST_TIMEOUT);
             return false;
@@ -109,6 +147,32 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, i
     asm volatile(
         "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
         ::"r"(smem_u32(dst)), "l"(map), "r"(x), "r"(y), "r"(smem_u32(bar))
+        : "memory");
+}
+// CTA pairs: rank in the cluster, peer addresses, remote arrive, cluster barrier
+__device__ __forceinline__ uint32_t cluster_rank() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+__device__ __forceinline__ uint32_t map_to_rank(uint32_t saddr, uint32_t rank) {
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(saddr), "r"(rank));
+    return r;
+}
+__device__ __forceinline__ void mbar_arrive_cluster(uint32_t cluster_addr) {
+    asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(cluster_addr) : "memory");
+}
+__device__ __forceinline__ void cluster_sync_all() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n barrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+// Pair form: the load lands in this CTA's shared memory and completes its
+// bytes on the mbarrier at a cluster address (the leader CTA's barrier).
+__device__ __forceinline__ void tma_load_2d_pair(void* dst, const CUtensorMap* map, int x, int y, uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.cta_group::2.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3}], [%4];"
+        ::"r"(smem_u32(dst)), "l"(map), "r"(x), "r"(y), "r"(bar)
         : "memory");
 }
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
@@ -129,32 +193,38 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
 __host__ __device__ constexpr uint32_t idesc_bf16(int m, int n) {
     return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
 }
+template <int CG>
 __device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
-    asm volatile(
-        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
-        ::"r"(d_tmem), "l"(a), "l"(b), "r"(idesc), "r"(acc));
+    if constexpr (CG == 1)
+        asm volatile(
+            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+            " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
+            ::"r"(d_tmem), "l"(a), "l"(b), "r"(idesc), "r"(acc));
+    else
+        asm volatile(
+            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+            " tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n}\n"
+            ::"r"(d_tmem), "l"(a), "l"(b), "r"(idesc), "r"(acc));
 }
+// Arrive on this CTA's barrier once the MMAs issued so far have completed.
+template <int CG>
 __device__ __forceinline__ void mma_commit(uint64_t* bar) {
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
-                 : "memory");
+    if constexpr (CG == 1)
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                     ::"r"(smem_u32(bar)) : "memory");
+    else
+        asm volatile("tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                     ::"r"(smem_u32(bar)) : "memory");
 }
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
-          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
-          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-        : "r"(taddr));
-}
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-        : "r"(taddr));
+// ... on the barrier at the same offset in every CTA of the pair.
+template <int CG>
+__device__ __forceinline__ void mma_commit_all(uint64_t* bar) {
+    if constexpr (CG == 1)
+        mma_commit<1>(bar);
+    else
+        asm volatile(
+            "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;"
+            ::"r"(smem_u32(bar)), "h"((unsigned short)3) : "memory");
 }
 __device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&r)[8]) {
     asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
@@ -206,11 +276,14 @@ struct MmaArgs {
     const int64_t* cons_n;
 };
 
-template <int S>
+template <int S, int CG>
 __global__ void __launch_bounds__(THREADS, 1)
 k_split_mma(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, const MmaArgs g) {
-    constexpr int STAGES = stages_for(S);
-    constexpr int STAGE_BYTES = 2 * S * TILE_BYTES;
+    constexpr int STAGES = stages_for(S, CG);
+    constexpr int STAGE_BYTES = stage_bytes_for(S, CG);
+    constexpr int B_TILE = b_tile_bytes(CG);
+    constexpr int TILE_M = BM * CG;                // output rows per tile (per CTA pair)
+    constexpr int B_ROWS = BN / CG;                // B columns this CTA stages
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint64_t* full = (uint64_t*)(smem + STAGES * STAGE_BYTES);
@@ -224,29 +297,45 @@ k_split_mma(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
 
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
-    const int tiles_m = (g.M + BM - 1) / BM;
+    const int tiles_m = (g.M + TILE_M - 1) / TILE_M;
     const int tiles_n = (g.N + BN - 1) / BN;
     const int num_tiles = tiles_m * tiles_n;
     const int num_kb = g.Kp / BK;
+    // a pair shares every tile: the leader (rank 0) issues the MMAs for both,
+    // and its barriers collect the loads and the drains of both CTAs
+    const uint32_t rank = CG == 2 ? cluster_rank() : 0u;
+    const int first_tile = (int)blockIdx.x / CG, tile_step = (int)gridDim.x / CG;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) { mbar_init(&full[s], 1); mbar_init(&empty[s], 1); }
         mbar_init(acc_full, 1);
-        mbar_init(acc_empty, EPI_WARPS);
+        mbar_init(acc_empty, EPI_WARPS * CG);
         mbar_init(mma_done, 1);
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
     if (warp == 1) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
-                     "r"(TMEM_COLS));
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+        if constexpr (CG == 1) {
+            asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                         ::"r"(smem_u32(tmem_slot)), "r"(TMEM_COLS));
+            asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+        } else {
+            // one warp of each CTA of the pair takes part
+            asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;"
+                         ::"r"(smem_u32(tmem_slot)), "r"(TMEM_COLS));
+            asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;");
+        }
     }
     tc_fence_before();
-    __syncthreads();
+    if constexpr (CG == 2)
+        cluster_sync_all();     // the peer's barriers are initialised before any remote arrive
+    else
+        __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
+    const uint32_t leader_full0 = CG == 2 ? map_to_rank(smem_u32(full), 0) : smem_u32(full);
+    const uint32_t leader_acc_empty = CG == 2 ? map_to_rank(smem_u32(acc_empty), 0) : smem_u32(acc_empty);
 
     if (warp == 0) {
         // ---------------------------------------------------------- TMA producer
@@ -257,16 +346,24 @@ k_split_mma(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
 #pragma unroll
             for (int s = 0; s < STAGES; ++s) issued[s] = -1;
             bool ok = true;
-            for (int tile = blockIdx.x; tile < num_tiles && ok; tile += gridDim.x) {
+            for (int tile = first_tile; tile < num_tiles && ok; tile += tile_step) {
                 const int mb = tile / tiles_n, nb = tile % tiles_n;
+                const int arow = mb * TILE_M + (int)rank * BM, brow = nb * BN + (int)rank * B_ROWS;
                 for (int kb = 0; kb < num_kb && ok; ++kb) {
                     ok = mbar_wait(&empty[stage], phase ^ 1, abort_flag, g.status);
                     if (!ok) break;
                     uint8_t* st = smem + stage * STAGE_BYTES;
-                    mbar_expect_tx(&full[stage], STAGE_BYTES);
+                    if (rank == 0) mbar_expect_tx(&full[stage], CG * STAGE_BYTES);   // both CTAs' bytes
                     for (int p = 0; p < S; ++p) {
-                        tma_load_2d(st + p * TILE_BYTES, &tmA, kb * BK, p * g.Mp + mb * BM, &full[stage]);
-                        tma_load_2d(st + (S + p) * TILE_BYTES, &tmB, kb * BK, p * g.Np + nb * BN, &full[stage]);
+                        if constexpr (CG == 1) {
+                            tma_load_2d(st + p * TILE_BYTES, &tmA, kb * BK, p * g.Mp + arow, &full[stage]);
+                            tma_load_2d(st + S * TILE_BYTES + p * B_TILE, &tmB, kb * BK, p * g.Np + brow,
+                                        &full[stage]);
+                        } else {
+                            const uint32_t bar = leader_full0 + (uint32_t)(stage * sizeof(uint64_t));
+                            tma_load_2d_pair(st + p * TILE_BYTES, &tmA, kb * BK, p * g.Mp + arow, bar);
+                            tma_load_2d_pair(st + S * TILE_BYTES + p * B_TILE, &tmB, kb * BK, p * g.Np + brow, bar);
+                        }
                     }
 #pragma unroll
                     for (int s = 0; s < STAGES; ++s)
@@ -274,66 +371,107 @@ k_split_mma(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
                     if (++stage == STAGES) { stage = 0; phase ^= 1; }
                 }
             }
-            // every load this thread issued has landed before the CTA may exit
-            // (bounded, and done even after an abort)
+            // every load issued has landed before the CTA may exit (bounded,
+            // and done even after an abort); the leader's barriers count the
+            // bytes of both CTAs of a pair
             volatile int never = 0;
+            if (rank == 0) {
 #pragma unroll
-            for (int s = 0; s < STAGES; ++s)
-                if (issued[s] >= 0) mbar_wait(&full[s], (uint32_t)issued[s], &never, g.status);
+                for (int s = 0; s < STAGES; ++s)
+                    if (issued[s] >= 0) mbar_wait(&full[s], (uint32_t)issued[s], &never, g.status);
+            }
         }
     } else if (warp == 1) {
         // ---------------------------------------------------------- MMA issuer
-        if (lane == 0) {
-            constexpr uint32_t IDESC = idesc_bf16(BM, BN);
+        if (lane == 0 && rank == 0) {
+            constexpr uint32_t IDESC = idesc_bf16(TILE_M, BN);
+            constexpr uint32_t IDESC_N256 = idesc_bf16(TILE_M, 2 * BN);
             const uint32_t acc0 = tmem, acc01 = tmem + 128, acc10 = tmem + 256, accr = tmem + 384;
             int stage = 0;
             uint32_t phase = 0;
             uint32_t chunk_no = 0;      // chunks issued so far (all tiles)
             bool ok = true;
-            for (int tile = blockIdx.x; tile < num_tiles && ok; tile += gridDim.x) {
+            for (int tile = first_tile; tile < num_tiles && ok; tile += tile_step) {
                 bool accr_started = false;
                 for (int kb = 0; kb < num_kb && ok; ++kb) {
                     const bool chunk_start = (kb % CHUNK_STAGES) == 0;
-                    if (chunk_start && chunk_no > 0) {
-                        // the epilogue must have drained the previous chunk
-                        ok = mbar_wait(acc_empty, (chunk_no - 1) & 1, abort_flag, g.status);
-                        if (!ok) break;
-                        tc_fence_after();
-                    }
+                    const bool tile_end = kb + 1 == num_kb;
+                    const bool chunk_end = ((kb + 1) % CHUNK_STAGES) == 0 || tile_end;
                     ok = mbar_wait(&full[stage], phase, abort_flag, g.status);
                     if (!ok) break;
                     tc_fence_after();
-                    const uint32_t base = smem_u32(smem + stage * STAGE_BYTES);
+                    // descriptors of this stage: one base, compile-time offsets
+                    // (start address in 16-byte units in the low 14 bits)
+                    const uint64_t dbase = smem_desc(smem_u32(smem + stage * STAGE_BYTES));
+                    // the exactly accumulated products (p + q <= 1) of this stage
+                    auto issue_exact = [&](bool first) {
 #pragma unroll
-                    for (int kk = 0; kk < BK / 16; ++kk) {
-                        const bool first_in_chunk = chunk_start && kk == 0;
+                        for (int kk = 0; kk < BK / 16; ++kk) {
+                            const uint32_t acc = (first && kk == 0) ? 0u : 1u;
+                            const uint64_t a0 = dbase + (uint64_t)((kk * 32) >> 4);
+                            const uint64_t a1 = dbase + (uint64_t)((TILE_BYTES + kk * 32) >> 4);
+                            const uint64_t b0 = dbase + (uint64_t)((S * TILE_BYTES + kk * 32) >> 4);
+                            const uint64_t b1 = dbase + (uint64_t)((S * TILE_BYTES + B_TILE + kk * 32) >> 4);
+                            if constexpr (CG == 1) {
+                                // B0 and B1 are adjacent 128-row tiles, ACC0 and ACC01
+                                // adjacent TMEM columns: one N = 256 product makes both
+                                mma_bf16<CG>(acc0, a0, b0, IDESC_N256, acc);
+                            } else {
+                                mma_bf16<CG>(acc0, a0, b0, IDESC, acc);
+                                mma_bf16<CG>(acc01, a0, b1, IDESC, acc);
+                            }
+                            mma_bf16<CG>(acc10, a1, b0, IDESC, acc);
+                        }
+                    };
+                    // the rest (2 <= p + q < S), into ACCR over the whole tile
+                    auto issue_rest = [&]() {
 #pragma unroll
-                        for (int p = 0; p < S; ++p) {
+                        for (int kk = 0; kk < BK / 16; ++kk) {
 #pragma unroll
-                            for (int q = 0; q + p < S; ++q) {
-                                const uint64_t da = smem_desc(base + p * TILE_BYTES + kk * 32);
-                                const uint64_t db = smem_desc(base + (S + q) * TILE_BYTES + kk * 32);
-                                uint32_t d;
-                                uint32_t accum;
-                                if (p + q == 0) { d = acc0; accum = first_in_chunk ? 0u : 1u; }
-                                else if (p == 0 && q == 1) { d = acc01; accum = first_in_chunk ? 0u : 1u; }
-                                else if (p == 1 && q == 0) { d = acc10; accum = first_in_chunk ? 0u : 1u; }
-                                else { d = accr; accum = accr_started ? 1u : 0u; accr_started = true; }
-                                mma_bf16(d, da, db, IDESC, accum);
+                            for (int p = 0; p < S; ++p) {
+#pragma unroll
+                                for (int q = 0; q + p < S; ++q) {
+                                    if (p + q < 2) continue;
+                                    const uint64_t da = dbase + (uint64_t)((p * TILE_BYTES + kk * 32) >> 4);
+                                    const uint64_t db = dbase + (uint64_t)((S * TILE_BYTES + q * B_TILE + kk * 32) >> 4);
+                                    mma_bf16<CG>(accr, da, db, IDESC, accr_started ? 1u : 0u);
+                                    accr_started = true;
+                                }
                             }
                         }
+                    };
+                    if (chunk_start && kb > 0) {
+                        // a drain of the exact accumulators inside this tile is
+                        // pending: keep the tensor pipe busy on ACCR meanwhile
+                        issue_rest();
+                        ok = mbar_wait(acc_empty, (chunk_no - 1) & 1, abort_flag, g.status);
+                        if (!ok) break;
+                        tc_fence_after();
+                        issue_exact(true);
+                    } else {
+                        if (chunk_start && chunk_no > 0) {
+                            // the previous tile's results (ACCR included) have been read
+                            ok = mbar_wait(acc_empty, (chunk_no - 1) & 1, abort_flag, g.status);
+                            if (!ok) break;
+                            tc_fence_after();
+                        }
+                        issue_exact(chunk_start);
+                        if (chunk_end && !tile_end) {
+                            mma_commit_all<CG>(acc_full);    // tracks the exact products only
+                            ++chunk_no;
+                        }
+                        issue_rest();
                     }
-                    mma_commit(&empty[stage]);
-                    const bool chunk_end = ((kb + 1) % CHUNK_STAGES) == 0 || kb + 1 == num_kb;
-                    if (chunk_end) {
-                        mma_commit(acc_full);
+                    mma_commit_all<CG>(&empty[stage]);
+                    if (tile_end) {
+                        mma_commit_all<CG>(acc_full);
                         ++chunk_no;
                     }
                     if (++stage == STAGES) { stage = 0; phase ^= 1; }
                 }
             }
             // every MMA issued has completed (also after an abort) ...
-            mma_commit(mma_done);
+            mma_commit<CG>(mma_done);
             volatile int never = 0;
             mbar_wait(mma_done, 0, &never, g.status);
             // ... and the last chunk has been drained before TMEM is released
@@ -349,8 +487,9 @@ k_split_mma(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
         const int nchunks = (num_kb + CHUNK_STAGES - 1) / CHUNK_STAGES;
         uint32_t chunk_no = 0;
         bool ok = true;
-        for (int tile = blockIdx.x; tile < num_tiles && ok; tile += gridDim.x) {
+        for (int tile = first_tile; tile < num_tiles && ok; tile += tile_step) {
             const int mb = tile / tiles_n, nb = tile % tiles_n;
+            const int row0 = mb * TILE_M + (int)rank * BM;   // this CTA's rows of the tile
             // J = I0 2^8 + I1: the exact ACC0 and ACC01 + ACC10 sums of this
             // tile's columns in one int64 each; at the end J becomes
             // V = J 2^14 + rint(ACCR 2^22) and then, in place, the FP64 bits
@@ -365,7 +504,7 @@ k_split_mma(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
                 if (!ok) break;
                 tc_fence_after();
                 const bool last = (c == nchunks - 1);
-                const int m = mb * BM + row_in_tile;
+                const int m = row0 + row_in_tile;
                 const bool row_ok = m < g.M;
                 const int ea = (last && row_ok) ? g.ea[m] : 0;
 #pragma unroll
@@ -434,7 +573,12 @@ k_split_mma(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
                 // TMEM is free for the next tile before the stores go out
                 tc_fence_before();
                 __syncwarp();
-                if (lane == 0) mbar_arrive(acc_empty);
+                if (lane == 0) {
+                    if constexpr (CG == 1)
+                        mbar_arrive(acc_empty);
+                    else
+                        mbar_arrive_cluster(leader_acc_empty);
+                }
                 ++chunk_no;
                 if (last) {
                     // stores through the warp's 32 x 8 staging tile: lanes of a
@@ -452,7 +596,7 @@ k_split_mma(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
 #pragma unroll 4
                         for (int q = 0; q < 8; ++q) {
                             const int rr = 4 * q + quarter;
-                            const int mr = mb * BM + quad * 32 + rr;
+                            const int mr = row0 + quad * 32 + rr;
                             if (mr < g.M && n < g.N) g.C[g.c_m[mr] + cn] = stg[rr * 8 + (cl ^ ((rr >> 1) & 7))];
                         }
                         __syncwarp();
@@ -462,12 +606,19 @@ k_split_mma(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
         }
     }
 
+    // no MMA of the pair is in flight and both CTAs have drained their TMEM
     tc_fence_before();
-    __syncthreads();
+    if constexpr (CG == 2)
+        cluster_sync_all();
+    else
+        __syncthreads();
     if (warp == 1) {
         __syncwarp();
         tc_fence_after();
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS));
+        if constexpr (CG == 1)
+            asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS));
+        else
+            asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS));
     }
 }
 
@@ -574,12 +725,12 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
     return fn;
 }
 
-CUtensorMap make_map(const void* base, int rows, int kp) {
+CUtensorMap make_map(const void* base, int rows, int kp, int box_rows = BM) {
     CUtensorMap m;
     std::memset(&m, 0, sizeof(m));
     const cuuint64_t dims[2] = {(cuuint64_t)kp, (cuuint64_t)rows};
     const cuuint64_t strides[1] = {(cuuint64_t)kp * 2};
-    const cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)BM};
+    const cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)box_rows};
     const cuuint32_t estr[2] = {1, 1};
     CUresult r = encode_fn()(&m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box,
                              estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
@@ -588,23 +739,56 @@ CUtensorMap make_map(const void* base, int rows, int kp) {
     return m;
 }
 
-template <int S>
+template <int S, int CG>
 void launch_mma(Ctx& ctx, const CUtensorMap& ta, const CUtensorMap& tb, const MmaArgs& a) {
     static std::once_flag once;
-    std::call_once(once, [] {
-        TRG_CUDA(cudaFuncSetAttribute(k_split_mma<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes_for(S)));
+    static int max_clusters = 0;
+    std::call_once(once, [&ctx] {
+        TRG_CUDA(cudaFuncSetAttribute(k_split_mma<S, CG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      smem_bytes_for(S, CG)));
+        if (CG == 2) {
+            // pairs that can be resident at once (a persistent grid must not exceed it)
+            cudaLaunchConfig_t cfg = {};
+            cudaLaunchAttribute attr[1];
+            attr[0].id = cudaLaunchAttributeClusterDimension;
+            attr[0].val.clusterDim.x = 2; attr[0].val.clusterDim.y = 1; attr[0].val.clusterDim.z = 1;
+            cfg.gridDim = dim3((unsigned)(ctx.sm_count & ~1));
+            cfg.blockDim = dim3(THREADS);
+            cfg.dynamicSmemBytes = smem_bytes_for(S, CG);
+            cfg.attrs = attr;
+            cfg.numAttrs = 1;
+            TRG_CUDA(cudaOccupancyMaxActiveClusters(&max_clusters, k_split_mma<S, CG>, &cfg));
+        }
     });
-    const int tiles = ((a.M + BM - 1) / BM) * ((a.N + BN - 1) / BN);
-    const int grid = std::max(1, std::min(tiles, ctx.sm_count));
-    k_split_mma<S><<<grid, THREADS, smem_bytes_for(S), ctx.stream>>>(ta, tb, a);
+    const int tiles = ((a.M + BM * CG - 1) / (BM * CG)) * ((a.N + BN - 1) / BN);
+    cudaError_t e;
+    if (CG == 1) {
+        const int grid = std::max(1, std::min(tiles, ctx.sm_count));
+        k_split_mma<S, CG><<<grid, THREADS, smem_bytes_for(S, CG), ctx.stream>>>(ta, tb, a);
+        e = cudaGetLastError();
+    } else {
+        if (max_clusters < 1) fail(TRG_ENOTSUP, "split MMA: no CTA pair fits on this device");
+        const int pairs = std::max(1, std::min(tiles, max_clusters));
+        cudaLaunchConfig_t cfg = {};
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = 2; attr[0].val.clusterDim.y = 1; attr[0].val.clusterDim.z = 1;
+        cfg.gridDim = dim3((unsigned)(2 * pairs));
+        cfg.blockDim = dim3(THREADS);
+        cfg.dynamicSmemBytes = smem_bytes_for(S, CG);
+        cfg.stream = ctx.stream;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        e = cudaLaunchKernelEx(&cfg, k_split_mma<S, CG>, ta, tb, a);
+        if (e == cudaSuccess) e = cudaGetLastError();
+    }
     ctx.launches++;
-    const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) {
         cudaFuncAttributes fa;
-        cudaFuncGetAttributes(&fa, k_split_mma<S>);
+        cudaFuncGetAttributes(&fa, k_split_mma<S, CG>);
         fail(TRG_ECUDA, std::string("split MMA launch: ") + cudaGetErrorString(e) + " (regs " +
                             std::to_string(fa.numRegs) + ", max threads " + std::to_string(fa.maxThreadsPerBlock) +
-                            ", dyn smem " + std::to_string(smem_bytes_for(S)) + " / " +
+                            ", dyn smem " + std::to_string(smem_bytes_for(S, CG)) + " / " +
                             std::to_string(fa.maxDynamicSharedSizeBytes) + ", local " +
                             std::to_string(fa.localSizeBytes) + ")");
     }
@@ -643,7 +827,10 @@ void gemm_split(Ctx& ctx, const GemmDesc& d) {
     if (d.M > (1ll << 30) || d.N > (1ll << 30) || d.K > (1 << 17)) fail(TRG_EINVAL, "split GEMM: size out of range");
     const int S = ctx.cfg.split_slices;
     const int M = (int)d.M, N = (int)d.N, K = (int)std::max<int64_t>(d.K, 1);
-    const int Mp = (M + BM - 1) / BM * BM, Np = (N + BN - 1) / BN * BN, Kp = (K + BK - 1) / BK * BK;
+    // CTA pairs (256-row tiles) once A has more than one 128-row block
+    const int CG = (ctx.cfg.mma_pairs && M > BM) ? 2 : 1;
+    const int Mp = (M + BM * CG - 1) / (BM * CG) * (BM * CG), Np = (N + BN - 1) / BN * BN,
+              Kp = (K + BK - 1) / BK * BK;
 
     // scratch: exponents + slices of A and B
     const size_t bytes_e = (size_t)(Mp + Np) * sizeof(int);
@@ -677,18 +864,22 @@ void gemm_split(Ctx& ctx, const GemmDesc& d) {
         default: fail(TRG_EINVAL, "split_slices must be 2..5");
     }
     const CUtensorMap ta = make_map(sa, S * Mp, Kp);
-    const CUtensorMap tb = make_map(sb, S * Np, Kp);
+    const CUtensorMap tb = make_map(sb, S * Np, Kp, BN / CG);
     MmaArgs a;
     a.M = M; a.N = N; a.Kp = Kp; a.Mp = Mp; a.Np = Np; a.S = S;
     a.ea = ea; a.eb = eb; a.C = d.C; a.c_m = d.c_m; a.c_n = d.c_n;
     a.status = ctx.status.as<int>();
     a.cons_ef = d.cons_ef; a.cons_m = d.cons_m; a.cons_n = d.cons_n;
     const int tok = ctx.region_begin(TRG_PHASE_MMA);
-    switch (S) {
-        case 2: launch_mma<2>(ctx, ta, tb, a); break;
-        case 3: launch_mma<3>(ctx, ta, tb, a); break;
-        case 4: launch_mma<4>(ctx, ta, tb, a); break;
-        case 5: launch_mma<5>(ctx, ta, tb, a); break;
+    switch (S * 2 + CG - 1) {
+        case 4: launch_mma<2, 1>(ctx, ta, tb, a); break;
+        case 5: launch_mma<2, 2>(ctx, ta, tb, a); break;
+        case 6: launch_mma<3, 1>(ctx, ta, tb, a); break;
+        case 7: launch_mma<3, 2>(ctx, ta, tb, a); break;
+        case 8: launch_mma<4, 1>(ctx, ta, tb, a); break;
+        case 9: launch_mma<4, 2>(ctx, ta, tb, a); break;
+        case 10: launch_mma<5, 1>(ctx, ta, tb, a); break;
+        case 11: launch_mma<5, 2>(ctx, ta, tb, a); break;
     }
     const double products = (double)S * (S + 1) / 2;
     ctx.region_end(tok, 2.0 * (double)M * N * K, products * 2.0 * (double)M * N * Kp);
@@ -829,9 +1020,9 @@ extern "C" int trg_gemm_noalloc(int M, int N, int K, const double* A, int lda, c
         const int grid = std::max(1, std::min(tiles, sms));
         switch (S) {
 #define TRG_NOALLOC_MMA(SS)                                                                                  \
-    TRG_CUDA(cudaFuncSetAttribute(k_split_mma<SS>, cudaFuncAttributeMaxDynamicSharedMemorySize,              \
-                                  smem_bytes_for(SS)));                                                      \
-    k_split_mma<SS><<<grid, THREADS, smem_bytes_for(SS), stream>>>(ta, tbm, a);                              \
+    TRG_CUDA(cudaFuncSetAttribute(k_split_mma<SS, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,           \
+                                  smem_bytes_for(SS, 1)));                                                   \
+    k_split_mma<SS, 1><<<grid, THREADS, smem_bytes_for(SS, 1), stream>>>(ta, tbm, a);                        \
     break;
             case 2: TRG_NOALLOC_MMA(2)
             case 3: TRG_NOALLOC_MMA(3)

@@ -60,6 +60,30 @@ def test_split_gemm_error_bound(torch, m, n, k, s):
     assert np.all(np.abs(c - ref) <= _bound(a, b, s))
 
 
+@pytest.mark.parametrize("m,n,k", [(130, 257, 100), (300, 70, 2100), (513, 128, 1100)])
+@pytest.mark.parametrize("s", [2, 3, 4, 5])
+def test_split_gemm_pairs_exact_on_integers(torch, m, n, k, s):
+    # the CTA-pair kernel (256-row tiles, cta_group::2) on the same exact cases
+    rng = np.random.default_rng(m * 11 + n * 5 + k + s)
+    a = rng.integers(-100, 101, size=(m, k)).astype(np.float64)
+    b = rng.integers(-100, 101, size=(k, n)).astype(np.float64)
+    with Solver(0, precision="split", split_slices=s, mma_pairs=1) as sv:
+        c = sv.gemm(torch.from_numpy(a).cuda(), torch.from_numpy(b).cuda()).cpu().numpy()
+    assert np.array_equal(c, a @ b)
+
+
+@pytest.mark.parametrize("m,n,k", [(257, 300, 4096), (1000, 129, 3000), (4096, 512, 2048)])
+def test_split_gemm_pairs_match_single(torch, m, n, k):
+    # same slices, same exact sums, same remainder order: identical bits
+    rng = np.random.default_rng(m + n + k)
+    a = torch.from_numpy(rng.standard_normal((m, k))).cuda()
+    b = torch.from_numpy(rng.standard_normal((k, n))).cuda()
+    with Solver(0, precision="split", mma_pairs=0) as s1, Solver(0, precision="split", mma_pairs=1) as s2:
+        c1 = s1.gemm(a, b)
+        c2 = s2.gemm(a, b)
+    assert torch.equal(c1, c2)
+
+
 def test_split_gemm_zero_rows_and_tiny_values(torch):
     a = np.zeros((40, 64))
     a[3] = 1e-300
@@ -82,12 +106,13 @@ def test_split_environment(torch, dx, dy):
     assert np.abs(m - ref).max() <= 1e-7 * np.abs(ref).max()
 
 
-@pytest.mark.parametrize("dx,dy,dn,ws", [(8, 8, 20, 0), (12, 7, 33, 0), (16, 16, 64, 3_000_000)])
-def test_split_contraction(torch, dx, dy, dn, ws):
+@pytest.mark.parametrize("dx,dy,dn,ws,pairs", [(8, 8, 20, 0, 0), (12, 7, 33, 0, 0), (16, 16, 64, 3_000_000, 0),
+                                               (16, 16, 64, 3_000_000, 1)])
+def test_split_contraction(torch, dx, dy, dn, ws, pairs):
     t = workloads.random_tensor((dx, dy, dx, dy), seed=600 + dx)
     u = workloads.random_isometry(dx, dn, seed=700 + dn)
     ref = hotrg.contract_x(t, u)
-    with Solver(0, precision="split", split_slices=4, workspace_bytes=ws) as sv:
+    with Solver(0, precision="split", split_slices=4, workspace_bytes=ws, mma_pairs=pairs) as sv:
         out = sv.contract(torch.from_numpy(t).cuda(), torch.from_numpy(u).cuda()).cpu().numpy()
     assert np.abs(out - ref).max() <= 1e-7 * np.abs(ref).max()
 
