@@ -179,6 +179,8 @@ static void half_step(Ctx& ctx, int dcut) {
 }
 
 static void reset_solve(Ctx& ctx) {
+    // a solve depends on its own inputs only, whatever the context ran before
+    ctx.eig_hint[0] = ctx.eig_hint[1] = Ctx::EigHint();
     ctx.have_tensor = false;
     ctx.steps = 0;
     ctx.spectra.clear();
@@ -479,6 +481,7 @@ int trg_isometry(trg_ctx* ctx, const double* M_dev, int n, int Dcut, double* U_d
         *dn_out = n;
     } else {
         std::vector<double> lam;
+        ctx->eig_hint[1] = trg::Ctx::EigHint();   // a component call starts from scratch
         const int dn = trg::isometry(*ctx, M_dev, n, Dcut, U_dev, lam, 1, ctx->cfg.precision);
         *dn_out = dn;
         if (lam_host) std::memcpy(lam_host, lam.data(), sizeof(double) * (size_t)dn);

@@ -88,79 +88,88 @@ __global__ void __launch_bounds__(256) k_col_normalize(double* Y, int64_t n, int
     for (int64_t r = threadIdx.x; r < n; r += 256) y[r] *= scale;
 }
 
-// Right-looking Cholesky G = L L^T of an m x m Gram matrix of unit columns
-// (the trailing updates run in parallel; FP64 latency, not throughput, is what
-// a column-at-a-time dot product would pay for).  A pivot d_j <= tau * G_jj
-// marks column j as dependent (flags[j] = 1, *nbad += 1); the pivot is then
-// replaced by G_jj so the factorisation can continue.
+// Right-looking Cholesky G = L L^T of an m x m Gram matrix of unit columns.
+// Per column: warp 0 takes the pivot and scales the column (also into a
+// broadcast copy), then every warp updates trailing rows, a lane per column.
+// A pivot d_j <= tau * G_jj marks column j as dependent (flags[j] = 1,
+// *nbad += 1); the pivot is then replaced by G_jj so the factorisation can
+// continue.
 __global__ void __launch_bounds__(256) k_chol_flag(const double* G, double* Lout, int m, double tau,
                                                    int* flags, int* nbad) {
-    extern __shared__ double L[];   // m*m, row-major, then m doubles of the original diagonal
+    extern __shared__ double L[];   // m*m row-major, m of the original diagonal, m of column j
     double* gd = L + m * m;
-    __shared__ double inv_ljj;
-    for (int e = threadIdx.x; e < m * m; e += 256) L[e] = G[e];
-    for (int i = threadIdx.x; i < m; i += 256) gd[i] = G[(int64_t)i * m + i];
+    double* colj = gd + m;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
+    for (int e = threadIdx.x; e < m * m; e += blockDim.x) L[e] = G[e];
+    for (int i = threadIdx.x; i < m; i += blockDim.x) gd[i] = G[(int64_t)i * m + i];
     __syncthreads();
     for (int j = 0; j < m; ++j) {
-        if (threadIdx.x == 0) {
+        if (warp == 0) {
             double d = L[j * m + j];
-            const double gjj = gd[j];
-            if (!(d > tau * gjj) || !isfinite(d)) {
-                flags[j] = 1;
-                atomicAdd(nbad, 1);
-                d = (gjj > 0.0 && isfinite(gjj)) ? gjj : 1.0;
+            if (lane == 0) {
+                const double gjj = gd[j];
+                if (!(d > tau * gjj) || !isfinite(d)) {
+                    flags[j] = 1;
+                    atomicAdd(nbad, 1);
+                    d = (gjj > 0.0 && isfinite(gjj)) ? gjj : 1.0;
+                }
             }
-            const double l = sqrt(d);
-            L[j * m + j] = l;
-            inv_ljj = 1.0 / l;
+            d = __shfl_sync(0xffffffffu, d, 0);
+            const double il = rsqrt(d);
+            if (lane == 0) L[j * m + j] = d * il;
+            for (int i = j + 1 + lane; i < m; i += 32) {
+                const double v = L[i * m + j] * il;
+                L[i * m + j] = v;
+                colj[i] = v;
+            }
         }
         __syncthreads();
-        const double il = inv_ljj;
-        for (int i = j + 1 + threadIdx.x; i < m; i += 256) L[i * m + j] *= il;
-        __syncthreads();
-        const int t = m - j - 1;
-        for (int e = threadIdx.x; e < t * t; e += 256) {
-            const int i = j + 1 + e / t, k = j + 1 + e % t;
-            if (k <= i) L[i * m + k] = fma(-L[i * m + j], L[k * m + j], L[i * m + k]);
+        for (int i = j + 1 + warp; i < m; i += nwarps) {
+            const double li = colj[i];
+            for (int k = j + 1 + lane; k <= i; k += 32) L[i * m + k] = fma(-li, colj[k], L[i * m + k]);
         }
         __syncthreads();
     }
-    for (int e = threadIdx.x; e < m * m; e += 256) Lout[e] = ((e % m) <= (e / m)) ? L[e] : 0.0;
+    for (int e = threadIdx.x; e < m * m; e += blockDim.x) Lout[e] = ((e % m) <= (e / m)) ? L[e] : 0.0;
 }
 
-// Q = Y L^{-T} row by row (forward substitution), in place allowed.  Each
-// thread keeps its row in shared memory (FP64 latency, not throughput, bounds
-// a dependent chain through global memory); four partial sums per dot.
-constexpr int TRSM_THREADS = 32;
+// Q = Y L^{-T} row by row, in place allowed: 32 rows per block, a lane per
+// row, the solution in shared memory.  Right-looking: after x_j is known,
+// every later column k subtracts L[k][j] x_j.  Column k belongs to warp
+// k % 4, so the four warps (and the SM's four FP64 pipes) share the updates
+// and x_j needs no reduction, one block barrier per column.
+constexpr int TRSM_ROWS = 32;
+constexpr int TRSM_THREADS = 128;
 __global__ void __launch_bounds__(TRSM_THREADS) k_trsm_rows(double* Y, const double* Lg, int64_t n, int m) {
-    extern __shared__ double L[];   // m*m, then m inverse diagonals, then TRSM_THREADS rows of m
+    extern __shared__ double L[];   // m*m, m inverse diagonals, TRSM_ROWS rows of m + 1, 2 x TRSM_ROWS x_j
     double* dinv = L + m * m;
     double* rows = dinv + m;
+    double* xb = rows + TRSM_ROWS * (m + 1);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     for (int e = threadIdx.x; e < m * m; e += blockDim.x) L[e] = Lg[e];
     for (int i = threadIdx.x; i < m; i += blockDim.x) dinv[i] = 1.0 / Lg[(int64_t)i * m + i];
-    const int64_t r0 = (int64_t)blockIdx.x * TRSM_THREADS;
-    for (int e = threadIdx.x; e < m * TRSM_THREADS; e += blockDim.x) {
-        const int j = e / TRSM_THREADS, t = e % TRSM_THREADS;
+    const int64_t r0 = (int64_t)blockIdx.x * TRSM_ROWS;
+    for (int e = threadIdx.x; e < m * TRSM_ROWS; e += blockDim.x) {
+        const int j = e / TRSM_ROWS, t = e % TRSM_ROWS;
         rows[t * (m + 1) + j] = (r0 + t < n) ? Y[(int64_t)j * n + r0 + t] : 0.0;
     }
     __syncthreads();
-    double* x = rows + threadIdx.x * (m + 1);
+    double* y = rows + lane * (m + 1);
     for (int j = 0; j < m; ++j) {
-        double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
-        const double* lj = L + j * m;
-        int k = 0;
-        for (; k + 3 < j; k += 4) {
-            s0 = fma(lj[k], x[k], s0);
-            s1 = fma(lj[k + 1], x[k + 1], s1);
-            s2 = fma(lj[k + 2], x[k + 2], s2);
-            s3 = fma(lj[k + 3], x[k + 3], s3);
+        double* xs = xb + (j & 1) * TRSM_ROWS;
+        if (warp == (j & 3)) {
+            const double x = y[j] * dinv[j];
+            y[j] = x;
+            xs[lane] = x;
         }
-        for (; k < j; ++k) s0 = fma(lj[k], x[k], s0);
-        x[j] = (x[j] - ((s0 + s1) + (s2 + s3))) * dinv[j];
+        __syncthreads();
+        const double x = xs[lane];
+        int k = j + 1 + ((warp - (j + 1)) & 3);      // first column > j owned by this warp
+        for (; k < m; k += 4) y[k] = fma(-L[k * m + j], x, y[k]);
     }
     __syncthreads();
-    for (int e = threadIdx.x; e < m * TRSM_THREADS; e += blockDim.x) {
-        const int j = e / TRSM_THREADS, t = e % TRSM_THREADS;
+    for (int e = threadIdx.x; e < m * TRSM_ROWS; e += blockDim.x) {
+        const int j = e / TRSM_ROWS, t = e % TRSM_ROWS;
         if (r0 + t < n) Y[(int64_t)j * n + r0 + t] = rows[t * (m + 1) + j];
     }
 }
@@ -218,9 +227,10 @@ __device__ __forceinline__ void rr_pair(int r, int i, int mp, int& p, int& q) {
 }
 
 template <typename T>
-__device__ int jacobi_sweeps(T* H, T* W, int m, T tol, int max_sweeps, T* cs, int* rot) {
+__device__ int jacobi_sweeps(T* H, T* W, int m, T tol, int max_sweeps, T* cs, int* rot, int* pq) {
     const int mp = m + (m & 1);            // even player count (dummy index m when odd)
     const int npair = mp / 2;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
     for (int sweep = 0; sweep < max_sweeps; ++sweep) {
         if (threadIdx.x == 0) *rot = 0;
         __syncthreads();
@@ -241,45 +251,43 @@ __device__ int jacobi_sweeps(T* H, T* W, int m, T tol, int max_sweeps, T* cs, in
                 }
                 cs[2 * i] = c;
                 cs[2 * i + 1] = s;
+                pq[2 * i] = p;
+                pq[2 * i + 1] = q;
             }
             __syncthreads();
-            // columns: H <- H J, W <- W J
-            for (int e = threadIdx.x; e < npair * m; e += blockDim.x) {
-                const int i = e / m, k = e % m;
+            // columns: H <- H J, W <- W J (a warp per rotation, a lane per row)
+            for (int i = warp; i < npair; i += nwarps) {
                 const T s = cs[2 * i + 1];
                 if (s == 0) continue;
                 const T c = cs[2 * i];
-                int p, q;
-                rr_pair(r, i, mp, p, q);
-                const T hkp = H[k * m + p], hkq = H[k * m + q];
-                H[k * m + p] = c * hkp - s * hkq;
-                H[k * m + q] = s * hkp + c * hkq;
+                const int p = pq[2 * i], q = pq[2 * i + 1];
                 T* wp = W + (int64_t)p * m;
                 T* wq = W + (int64_t)q * m;
-                const T vp = wp[k], vq = wq[k];
-                wp[k] = c * vp - s * vq;
-                wq[k] = s * vp + c * vq;
+                for (int k = lane; k < m; k += 32) {
+                    const T hkp = H[k * m + p], hkq = H[k * m + q];
+                    H[k * m + p] = c * hkp - s * hkq;
+                    H[k * m + q] = s * hkp + c * hkq;
+                    const T vp = wp[k], vq = wq[k];
+                    wp[k] = c * vp - s * vq;
+                    wq[k] = s * vp + c * vq;
+                }
             }
             __syncthreads();
-            // rows: H <- J^T H
-            for (int e = threadIdx.x; e < npair * m; e += blockDim.x) {
-                const int i = e / m, k = e % m;
+            // rows: H <- J^T H, then the annihilated pair is exactly zero
+            for (int i = warp; i < npair; i += nwarps) {
                 const T s = cs[2 * i + 1];
                 if (s == 0) continue;
                 const T c = cs[2 * i];
-                int p, q;
-                rr_pair(r, i, mp, p, q);
-                const T hpk = H[p * m + k], hqk = H[q * m + k];
-                H[p * m + k] = c * hpk - s * hqk;
-                H[q * m + k] = s * hpk + c * hqk;
-            }
-            __syncthreads();
-            for (int i = threadIdx.x; i < npair; i += blockDim.x) {
-                if (cs[2 * i + 1] == 0) continue;
-                int p, q;
-                rr_pair(r, i, mp, p, q);
-                H[p * m + q] = 0;
-                H[q * m + p] = 0;
+                const int p = pq[2 * i], q = pq[2 * i + 1];
+                T* hp = H + p * m;
+                T* hq = H + q * m;
+                for (int k = lane; k < m; k += 32) {
+                    const T hpk = hp[k], hqk = hq[k];
+                    hp[k] = c * hpk - s * hqk;
+                    hq[k] = s * hpk + c * hqk;
+                }
+                __syncwarp();
+                if (lane == 0) { hp[q] = 0; hq[p] = 0; }
             }
             __syncthreads();
         }
@@ -314,6 +322,7 @@ __global__ void __launch_bounds__(512) k_jacobi(const double* Hg, int m, double 
     float* cs32 = (float*)(cs64 + mp);         // mp
     int* rot = (int*)(cs32 + mp + (mp & 1));   // 1
     int* perm = rot + 2;                       // m
+    int* pq = perm + m + (m & 1);              // mp: the pairs of the current round
     __shared__ double hmax_s;
     if (threadIdx.x == 0) hmax_s = 0.0;
     __syncthreads();
@@ -334,7 +343,7 @@ __global__ void __launch_bounds__(512) k_jacobi(const double* Hg, int m, double 
     }
     __syncthreads();
     // 1. FP32 sweeps
-    const int s32 = jacobi_sweeps<float>(H32, W32, m, 1e-6f, 40, cs32, rot);
+    const int s32 = jacobi_sweeps<float>(H32, W32, m, 1e-6f, 40, cs32, rot, pq);
     // 2. W (FP64) = W32, then Cholesky-QR of its columns
     for (int e = threadIdx.x; e < m * m; e += blockDim.x) Wout[e] = (double)W32[e];
     __syncthreads();
@@ -391,7 +400,7 @@ __global__ void __launch_bounds__(512) k_jacobi(const double* Hg, int m, double 
     __syncthreads();
     // 3. FP64 sweeps (skipped for a rough Rayleigh-Ritz far from convergence:
     //    then theta is the diagonal of H' and W the re-orthonormalised W32)
-    const int s64 = fp64_sweeps ? jacobi_sweeps<double>(H, Wout, m, tol, max_sweeps, cs64, rot) : 0;
+    const int s64 = fp64_sweeps ? jacobi_sweeps<double>(H, Wout, m, tol, max_sweeps, cs64, rot, pq) : 0;
     if (threadIdx.x == 0) {
         if (s64 > max_sweeps) atomicOr(status, ST_EIG_NOCONV);
         if (sweeps_out) { atomicAdd(sweeps_out, s32); atomicAdd(sweeps_out + 1, s64); }
@@ -444,7 +453,11 @@ __global__ void k_to_isometry(const double* QW, int64_t n, int dn, double* U) {
 
 static size_t jacobi_smem(int m) {
     const int mp = m + (m & 1);
-    return (size_t)2 * m * m * 8 + (size_t)mp * 8 + (size_t)(mp + 2) * 4 + (size_t)(m + 4) * 4 + 64;
+    return (size_t)2 * m * m * 8 + (size_t)mp * 8 + (size_t)(mp + 2) * 4 + (size_t)(m + 4) * 4 + (size_t)mp * 4 + 64;
+}
+
+static size_t trsm_smem(int m) {
+    return (size_t)m * m * 8 + (size_t)m * 8 + (size_t)TRSM_ROWS * (m + 1) * 8 + 2 * TRSM_ROWS * 8;
 }
 
 static void set_smem(const void* fn, size_t bytes) {
@@ -489,8 +502,8 @@ static void orthonormalise(Ctx& ctx, double* Y, int64_t n, int m, double* G, dou
             k_col_normalize<<<m, 256, 0, ctx.stream>>>(Y, n, flags);
             TRG_LAUNCHED(ctx);
             gram(ctx, Y, Y, n, m, G, TRG_FP64);
-            k_chol_flag<<<1, 256, smem + (size_t)m * 8, ctx.stream>>>(G, L, m, pass == 0 ? 1e-8 : 1e-12, flags,
-                                                                     nbad);
+            k_chol_flag<<<1, 256, smem + (size_t)m * 16, ctx.stream>>>(G, L, m, pass == 0 ? 1e-8 : 1e-12, flags,
+                                                                      nbad);
             TRG_LAUNCHED(ctx);
             int hb = 0;
             TRG_CUDA(cudaMemcpyAsync(&hb, nbad, sizeof(int), cudaMemcpyDeviceToHost, ctx.stream));
@@ -502,8 +515,8 @@ static void orthonormalise(Ctx& ctx, double* Y, int64_t n, int m, double* G, dou
             k_rand_cols<<<grid, 256, 0, ctx.stream>>>(Y, n, m, flags, seed, ++salt);
             TRG_LAUNCHED(ctx);
         }
-        k_trsm_rows<<<(unsigned)((n + TRSM_THREADS - 1) / TRSM_THREADS), TRSM_THREADS,
-                      smem + (size_t)m * 8 + (size_t)TRSM_THREADS * (m + 1) * 8, ctx.stream>>>(Y, L, n, m);
+        k_trsm_rows<<<(unsigned)((n + TRSM_ROWS - 1) / TRSM_ROWS), TRSM_THREADS, trsm_smem(m), ctx.stream>>>(Y, L, n,
+                                                                                                          m);
         TRG_LAUNCHED(ctx);
     }
 }
@@ -515,8 +528,8 @@ int isometry(Ctx& ctx, const double* M, int64_t n, int dcut, double* U, std::vec
     if (m > MAX_M) fail(TRG_ENOTSUP, "isometry: Dcut + oversampling exceeds the supported block (112)");
     static std::once_flag once;
     std::call_once(once, [] {
-        set_smem((const void*)k_chol_flag, (size_t)MAX_M * MAX_M * 8 + MAX_M * 8);
-        set_smem((const void*)k_trsm_rows, (size_t)MAX_M * MAX_M * 8 + MAX_M * 8 + TRSM_THREADS * (MAX_M + 1) * 8);
+        set_smem((const void*)k_chol_flag, (size_t)MAX_M * MAX_M * 8 + MAX_M * 16);
+        set_smem((const void*)k_trsm_rows, trsm_smem(MAX_M));
         set_smem((const void*)k_jacobi, jacobi_smem(MAX_M));
     });
     // buffers: Q, Y, Z, QW (n x m each); G, L, W (m x m); theta (m)
@@ -555,12 +568,21 @@ int isometry(Ctx& ctx, const double* M, int64_t n, int dcut, double* U, std::vec
         gemm(ctx, g, precision);
     };
     orthonormalise(ctx, Q, n, m, G, L, flags, nbad, seed, salt);
-    // two plain block power steps before the first Rayleigh-Ritz: the random
-    // start is mostly noise, and the Jacobi solve of a dense H is the costly part
-    for (int pre = 0; pre < 2 && m < n; ++pre) {
-        apply_m();
-        std::swap(Q, Y);
-        orthonormalise(ctx, Q, n, m, G, L, flags, nbad, seed, salt);
+    // The number of products that reached the tolerance in the previous solve
+    // of this direction (same sizes) is the plan: the spectra of successive
+    // same-direction environments are close, and a random start needs about
+    // as many products each time.  Without one, two plain power steps precede
+    // a first, FP32-only Rayleigh-Ritz that measures the convergence rate.
+    Ctx::EigHint& hint = ctx.eig_hint[step & 1];
+    const bool have_hint = hint.n == n && hint.m == m && hint.precision == precision && hint.products > 0;
+    int applied = 0;                 // products of M in the span of Q
+    if (!have_hint) {
+        for (int pre = 0; pre < 2 && m < n; ++pre) {
+            apply_m();
+            std::swap(Q, Y);
+            orthonormalise(ctx, Q, n, m, G, L, flags, nbad, seed, salt);
+            ++applied;
+        }
     }
 
     const size_t jac_smem = jacobi_smem(m);
@@ -576,8 +598,8 @@ int isometry(Ctx& ctx, const double* M, int64_t n, int dcut, double* U, std::vec
     // residual and the convergence rate rho ~ theta_m / theta_dn; the power
     // steps needed to reach the tolerance follow from rho and run without a
     // Rayleigh-Ritz; the next (full FP64) one normally converges.
-    int pending = 0;                 // planned plain power steps
-    int rr_done = 0;
+    int pending = have_hint ? std::min(hint.products, 60) : 0;   // planned plain power steps
+    int rr_done = have_hint ? 1 : 0;
     double prev_res = 0.0;
     int since_rr = 0;                // products applied since the previous Rayleigh-Ritz
     for (int it = 1; it <= max_it; ++it) {
@@ -587,6 +609,7 @@ int isometry(Ctx& ctx, const double* M, int64_t n, int dcut, double* U, std::vec
             orthonormalise(ctx, Q, n, m, G, L, flags, nbad, seed, salt);
             --pending;
             ++since_rr;
+            ++applied;
             ctx.counters[0] += 1;
             continue;
         }
@@ -616,6 +639,14 @@ int isometry(Ctx& ctx, const double* M, int64_t n, int dcut, double* U, std::vec
         if (read_status(ctx) & ST_EIG_NOCONV) fail(TRG_ENUMERIC, "Rayleigh-Ritz Jacobi did not converge");
         if (!(th[0] > 0.0) || !std::isfinite(th[0])) fail(TRG_ENUMERIC, "environment has no positive eigenvalue");
         if ((res <= tol && full) || m == n) {
+            {
+                // products beyond what the tolerance needed (at the rate
+                // theta_m / theta_dn) are dropped from the next plan, one kept spare
+                const double r = std::min(std::max(th[(size_t)m - 1] / th[(size_t)dn_paper - 1], 0.05), 0.98);
+                const int slack = (res > 0.0 && res < tol) ? (int)std::floor(std::log(tol / res) / -std::log(r)) : 0;
+                hint.n = n; hint.m = m; hint.precision = precision;
+                hint.products = std::max(1, applied - std::max(0, slack - 1));
+            }
             int dn = dn_paper;
             if (ctx.cfg.trunc == TRG_TRUNC_MULTIPLET && dn < n) {
                 // split products separate exactly degenerate eigenvalues by up
@@ -642,6 +673,7 @@ int isometry(Ctx& ctx, const double* M, int64_t n, int dcut, double* U, std::vec
         prev_res = res;
         since_rr = 1;
         // next block: orth(Y W) = orth(M Q W), same span as M Q
+        ++applied;
         std::swap(Q, Z);
         orthonormalise(ctx, Q, n, m, G, L, flags, nbad, seed, salt);
     }

@@ -94,6 +94,10 @@ struct Ctx {
     // diagnostics: subspace iterations, Rayleigh-Ritz solves, FP32 / FP64
     // Jacobi sweeps, Cholesky-QR column repairs
     uint64_t counters[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    // Subspace iteration: power steps that reached the tolerance in the last
+    // solve of each direction (x / y half-steps), used as the next plan.
+    struct EigHint { int64_t n = -1; int m = -1; int precision = -1; int products = 0; };
+    EigHint eig_hint[2];
     cudaEvent_t get_event();
     // Record the start of a timed region of phase p (no-op unless profiling).
     int region_begin(int p);

@@ -233,6 +233,16 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&r)[8]) {
 }
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
+// rint(x) as int64 for |x| < 2^46 with 32-bit conversions only (the 64-bit
+// conversion runs on the FP64 pipe, 1/64 of the FP32 rate on this part):
+// hf = rint(x 2^-16) and the remainder x - hf 2^16 are both exact in FP32,
+// and rint(x) = hf 2^16 + rint(remainder) since hf 2^16 is an even integer.
+__device__ __forceinline__ long long rint_f32_to_i64(float x) {
+    const float hf = rintf(x * (1.0f / 65536.0f));
+    const int lo = __float2int_rn(fmaf(-hf, 65536.0f, x));
+    return ((long long)__float2int_rn(hf) << 16) + lo;
+}
+
 // Exact int64 -> FP64 bits times 2^e2, round-to-nearest-even, integer
 // operations only.  Results below the normal range (|value| < 2^-1022, far
 // under any entry that matters next to a normalised tensor) flush to zero.
@@ -524,7 +534,7 @@ k_split_mma(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
 #pragma unroll
                     for (int j = 0; j < 8; ++j) J[h * 8 + j] += __float2int_rn(__uint_as_float(r[j]) * 256.0f);
                     if (last) {
-                        // fold in ACCR and form these columns' FP64 results in place
+                        // fold in ACCR: J becomes V = J 2^14 + rint(ACCR 2^22)
                         if (S >= 3) {
                             tmem_ld8(tmem + lane_base + 384 + col, r);
                             tmem_wait_ld();
@@ -533,44 +543,13 @@ k_split_mma(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
 #pragma unroll
                             for (int j = 0; j < 8; ++j) r[j] = 0u;
                         }
-                        const int n0 = nb * BN + (int)col;
 #pragma unroll
-                        for (int j = 0; j < 8; ++j) {
-                            const int n = n0 + j;
-                            double v = 0.0;
-                            if (row_ok && n < g.N) {
-                                const long long iv = (J[h * 8 + j] << 14) +
-                                                     __float2ll_rn(__uint_as_float(r[j]) * 4194304.0f);
-                                v = scaled_i64_to_double(iv, ea + g.eb[n] - 36);
-                            }
-                            J[h * 8 + j] = __double_as_longlong(v);
-                        }
+                        for (int j = 0; j < 8; ++j)
+                            J[h * 8 + j] = (J[h * 8 + j] << 14) + rint_f32_to_i64(__uint_as_float(r[j]) * 4194304.0f);
                     }
                 }
-                if (last && g.cons_ef && row_ok) {
-                    // exponent fields of the consumer's rows: run-length maxima
-                    // over this thread's columns, one atomic per run
-                    const int64_t cm0 = g.cons_m[m];
-                    int64_t cur = -1;
-                    int cur_max = 0;
-#pragma unroll
-                    for (int j = 0; j < CPT; ++j) {
-                        const int n = nb * BN + colh * CPT + j;
-                        if (n < g.N) {
-                            const int64_t crow = cm0 + g.cons_n[n];
-                            const int ef = (int)(((unsigned long long)J[j] >> 52) & 0x7FF);
-                            if (crow != cur) {
-                                if (cur >= 0 && cur_max) atomicMax(&g.cons_ef[cur], cur_max);
-                                cur = crow;
-                                cur_max = ef;
-                            } else {
-                                cur_max = max(cur_max, ef);
-                            }
-                        }
-                    }
-                    if (cur >= 0 && cur_max) atomicMax(&g.cons_ef[cur], cur_max);
-                }
-                // TMEM is free for the next tile before the stores go out
+                // TMEM is free for the next tile before the FP64 results are
+                // formed and stored
                 tc_fence_before();
                 __syncwarp();
                 if (lane == 0) {
@@ -581,6 +560,38 @@ k_split_mma(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
                 }
                 ++chunk_no;
                 if (last) {
+                    // the FP64 results, in place
+                    const int nt = nb * BN + colh * CPT;
+#pragma unroll
+                    for (int j = 0; j < CPT; ++j) {
+                        const int n = nt + j;
+                        double v = 0.0;
+                        if (row_ok && n < g.N) v = scaled_i64_to_double(J[j], ea + g.eb[n] - 36);
+                        J[j] = __double_as_longlong(v);
+                    }
+                    if (g.cons_ef && row_ok) {
+                        // exponent fields of the consumer's rows: run-length maxima
+                        // over this thread's columns, one atomic per run
+                        const int64_t cm0 = g.cons_m[m];
+                        int64_t cur = -1;
+                        int cur_max = 0;
+#pragma unroll
+                        for (int j = 0; j < CPT; ++j) {
+                            const int n = nt + j;
+                            if (n < g.N) {
+                                const int64_t crow = cm0 + g.cons_n[n];
+                                const int ef = (int)(((unsigned long long)J[j] >> 52) & 0x7FF);
+                                if (crow != cur) {
+                                    if (cur >= 0 && cur_max) atomicMax(&g.cons_ef[cur], cur_max);
+                                    cur = crow;
+                                    cur_max = ef;
+                                } else {
+                                    cur_max = max(cur_max, ef);
+                                }
+                            }
+                        }
+                        if (cur >= 0 && cur_max) atomicMax(&g.cons_ef[cur], cur_max);
+                    }
                     // stores through the warp's 32 x 8 staging tile: lanes of a
                     // quarter-warp then write 8 adjacent columns (64 B) of one row
                     double* stg = staging + ew * (32 * 8);
