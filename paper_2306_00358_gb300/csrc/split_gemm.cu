@@ -9,15 +9,15 @@
 // as d_p 2^(-8p), exact (at most 8 significant bits), so
 //     x = 2^(e - 7) sum_p slice_p   and
 //     sum_k a_k b_k ~= 2^(ea + eb - 14) sum_{p + q < S} (A_p B_q^T).
-// Products of BF16 values are exact in FP32, and with |d_0 e_0|, |d_0 e_1|,
-// |d_1 e_0| <= 2^14 a run of 1024 of them sums exactly in an FP32
-// accumulator (|sum| <= 2^24).  The tensor cores therefore accumulate
-//   ACC0  = (0,0),  ACC01 = (0,1),  ACC10 = (1,0)   exactly over 1024-K chunks,
-//   ACCR  = all (p,q) with 2 <= p+q < S             in FP32 over the whole K
-// (ACCR carries weight <= 2^-16 relative to ACC0, so its FP32 rounding stays
+// Products of BF16 values are exact in FP32.  With |d_0 e_0| <= 2^14 and
+// |d_0 e_1| + |d_1 e_0| <= 2^15, runs of 512 K sum exactly in FP32 (|sum| <=
+// 2^24), so the tensor cores accumulate
+//   ACC0 = (0,0)            and  ACC1 = (0,1) + (1,0)   exactly over 512-K chunks,
+//   R, R2 = the products with 2 <= p+q < S               in FP32 over the whole K
+// (these carry weight <= 2^-16 relative to ACC0, so their FP32 rounding stays
 // below the truncation error).  After every chunk the epilogue warps move
-// ACC0 and ACC01 + ACC10 into int32 registers; at the end of a tile the sum
-//   V = I0 2^22 + I1 2^14 + rint(ACCR 2^22)      (int64, exact)
+// ACC0 and ACC1 into an int64 per column; at the end of a tile the sum
+//   V = I0 2^22 + I1 2^14 + rint(R 2^22) + rint(R2 2^22)      (int64, exact)
 // is turned into the FP64 result V 2^(ea + eb - 36) with integer operations,
 // keeping the FP64 pipe (1/64 of the FP32 rate on this part) out of the loop.
 //
@@ -25,14 +25,15 @@
 // operand tiles of 128 x 32 staged by TMA (64-byte swizzle) through an
 // mbarrier pipeline; warp 0 issues TMA, warp 1 owns TMEM and issues
 // tcgen05.mma (one thread), 16 epilogue warps drain TMEM (four per 32-lane
-// quadrant, 32 columns each).  Per 16-wide K step the exact products are one
-// N = 256 MMA (A0 against the adjacent B0|B1 tiles, into the adjacent ACC0|
-// ACC01 columns) and one N = 128 MMA (A1 B0); the remainder products are
-// issued while the epilogue drains a finished 1024-K chunk, so the tensor
-// pipe keeps working across the drain.  Waiting threads are suspended in
-// mbarrier.try_wait rather than spinning (spinning costs shared-memory
-// cycles that the MMA operand reads need).  Every wait is bounded: on
-// expiry the kernel records ST_TIMEOUT and leaves its loops.
+// quadrant, 32 columns each).  The single issuing thread, not the tensor
+// pipe, limits a stream of 128 x 128 x 16 MMAs, so products that share an A
+// slice and land in adjacent accumulators are issued as one N = 256 MMA
+// (see ins_of: 6 instructions for the 10 products of four slices).  The
+// remainder products are issued while the epilogue drains a finished chunk,
+// so the tensor pipe keeps working across the drain.  Waiting threads are
+// suspended in mbarrier.try_wait rather than spinning (spinning costs
+// shared-memory cycles that the MMA operand reads need).  Every wait is
+// bounded: on expiry the kernel records ST_TIMEOUT and leaves its loops.
 //
 // A second instance runs each 256 x 128 tile on a CTA pair (cta_group::2):
 // each CTA stages its own 128 rows of A and half of B, the even CTA issues
@@ -56,7 +57,7 @@ constexpr int BM = 128;
 constexpr int BN = 128;
 constexpr int BK = 32;                        // K per stage: 64 bytes of BF16
 constexpr int TILE_BYTES = BM * BK * 2;       // 8 KB per 128 x 32 BF16 tile
-constexpr int CHUNK_STAGES = 1024 / BK;       // exact-accumulation run (1024 K)
+constexpr int CHUNK_STAGES = 512 / BK;        // exact-accumulation run (512 K)
 constexpr int EPI_WARPS = 16;
 constexpr int THREADS = 64 + 32 * EPI_WARPS;  // TMA warp + MMA warp + epilogue
 constexpr uint32_t TMEM_COLS = 512;
@@ -284,7 +285,80 @@ struct MmaArgs {
     int* cons_ef;              // optional: exponent fields of the consumer's rows
     const int64_t* cons_m;
     const int64_t* cons_n;
+    int group_n;               // tile order: column blocks per group (see tile_coords)
 };
+
+// Tile order: column blocks in groups of group_n; inside a group the tiles run
+// row block by row block.  The CTAs of one wave then share about
+// grid / group_n row blocks of A and group_n column blocks of B, a working
+// set the host sizes to stay in L2 (a plain row-major order over many column
+// blocks streams all of B through L2 once per wave).
+__device__ __forceinline__ void tile_coords(int tile, int tiles_m, int tiles_n, int group_n, int& mb, int& nb) {
+    const int per_group = tiles_m * group_n;
+    const int group = tile / per_group;
+    const int first_n = group * group_n;
+    const int width = min(group_n, tiles_n - first_n);
+    const int local = tile - group * per_group;
+    mb = local / width;
+    nb = first_n + local % width;
+}
+
+// The slice products of one 16-wide K step, as tcgen05.mma instructions.
+// TMEM holds four 128-column accumulators, ACC0 | ACC1 | R | R2:
+//   ACC0 = A0 B0 and ACC1 = A0 B1 + A1 B0, exact over 512-K chunks and drained
+//   into int64 after each chunk; R and R2 = FP32 sums of the remaining
+//   products (2 <= p + q < S) over the whole tile.
+// Slices are stored with their weights (slice p = d_p 2^-8p), so a remainder
+// product may go to either of R and R2; the assignment below lets one N = 256
+// instruction cover A_p [B_q | B_q+1] (adjacent smem tiles) when its two
+// results land in adjacent accumulators, which cuts the instruction count the
+// single issuing thread has to sustain (S = 4: 6 instructions for 10 products).
+// flag: 0 = reset at a chunk start, 1 = reset at a tile start, 2 = accumulate.
+// Group 1 (touches ACC0 / ACC1, or initialises R) precedes group 2 except at a
+// chunk start inside a tile, where group 2 runs while the epilogue drains.
+struct SliceIns { int a, b, wide, col, flag, group; };
+__host__ __device__ constexpr int ins_count(int S) { return S == 2 ? 2 : S == 3 ? 4 : S == 4 ? 6 : 9; }
+__host__ __device__ constexpr SliceIns ins_of(int S, int t) {
+    // common head: A0 [B0|B1] -> ACC0|ACC1, then (S >= 3) R initialised by A2 B0
+    // (with A2 B1 into R2 when S >= 4), then A1 [B0|B1] -> ACC1|R
+    return S == 2 ? (t == 0 ? SliceIns{0, 0, 1, 0, 0, 1} : SliceIns{1, 0, 0, 128, 2, 1})
+         : S == 3 ? (t == 0 ? SliceIns{0, 0, 1, 0, 0, 1}
+                   : t == 1 ? SliceIns{2, 0, 0, 256, 1, 1}
+                   : t == 2 ? SliceIns{1, 0, 1, 128, 2, 1}
+                            : SliceIns{0, 2, 0, 256, 2, 2})
+         : S == 4 ? (t == 0 ? SliceIns{0, 0, 1, 0, 0, 1}
+                   : t == 1 ? SliceIns{2, 0, 1, 256, 1, 1}
+                   : t == 2 ? SliceIns{1, 0, 1, 128, 2, 1}
+                   : t == 3 ? SliceIns{0, 2, 1, 256, 2, 2}
+                   : t == 4 ? SliceIns{1, 2, 0, 384, 2, 2}
+                            : SliceIns{3, 0, 0, 384, 2, 2})
+                  : (t == 0 ? SliceIns{0, 0, 1, 0, 0, 1}
+                   : t == 1 ? SliceIns{2, 0, 1, 256, 1, 1}
+                   : t == 2 ? SliceIns{1, 0, 1, 128, 2, 1}
+                   : t == 3 ? SliceIns{0, 2, 1, 256, 2, 2}
+                   : t == 4 ? SliceIns{1, 2, 1, 256, 2, 2}
+                   : t == 5 ? SliceIns{3, 0, 1, 256, 2, 2}
+                   : t == 6 ? SliceIns{2, 2, 0, 384, 2, 2}
+                   : t == 7 ? SliceIns{0, 4, 0, 384, 2, 2}
+                            : SliceIns{4, 0, 0, 384, 2, 2});
+}
+// Every product p + q < S exactly once, and no other (checked at compile time).
+__host__ __device__ constexpr bool ins_cover_ok(int S) {
+    int seen[5][5] = {};
+    for (int t = 0; t < ins_count(S); ++t) {
+        const SliceIns in = ins_of(S, t);
+        seen[in.a][in.b] += 1;
+        if (in.wide) {
+            if (in.b + 1 >= S) return false;
+            seen[in.a][in.b + 1] += 1;
+        }
+    }
+    for (int p = 0; p < 5; ++p)
+        for (int q = 0; q < 5; ++q)
+            if (seen[p][q] != ((p < S && q < S && p + q < S) ? 1 : 0)) return false;
+    return true;
+}
+static_assert(ins_cover_ok(2) && ins_cover_ok(3) && ins_cover_ok(4) && ins_cover_ok(5), "slice product table");
 
 template <int S, int CG>
 __global__ void __launch_bounds__(THREADS, 1)
@@ -357,7 +431,8 @@ k_split_mma(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
             for (int s = 0; s < STAGES; ++s) issued[s] = -1;
             bool ok = true;
             for (int tile = first_tile; tile < num_tiles && ok; tile += tile_step) {
-                const int mb = tile / tiles_n, nb = tile % tiles_n;
+                int mb, nb;
+                tile_coords(tile, tiles_m, tiles_n, g.group_n, mb, nb);
                 const int arow = mb * TILE_M + (int)rank * BM, brow = nb * BN + (int)rank * B_ROWS;
                 for (int kb = 0; kb < num_kb && ok; ++kb) {
                     ok = mbar_wait(&empty[stage], phase ^ 1, abort_flag, g.status);
@@ -396,13 +471,11 @@ k_split_mma(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
         if (lane == 0 && rank == 0) {
             constexpr uint32_t IDESC = idesc_bf16(TILE_M, BN);
             constexpr uint32_t IDESC_N256 = idesc_bf16(TILE_M, 2 * BN);
-            const uint32_t acc0 = tmem, acc01 = tmem + 128, acc10 = tmem + 256, accr = tmem + 384;
             int stage = 0;
             uint32_t phase = 0;
             uint32_t chunk_no = 0;      // chunks issued so far (all tiles)
             bool ok = true;
             for (int tile = first_tile; tile < num_tiles && ok; tile += tile_step) {
-                bool accr_started = false;
                 for (int kb = 0; kb < num_kb && ok; ++kb) {
                     const bool chunk_start = (kb % CHUNK_STAGES) == 0;
                     const bool tile_end = kb + 1 == num_kb;
@@ -413,64 +486,52 @@ k_split_mma(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
                     // descriptors of this stage: one base, compile-time offsets
                     // (start address in 16-byte units in the low 14 bits)
                     const uint64_t dbase = smem_desc(smem_u32(smem + stage * STAGE_BYTES));
-                    // the exactly accumulated products (p + q <= 1) of this stage
-                    auto issue_exact = [&](bool first) {
-#pragma unroll
-                        for (int kk = 0; kk < BK / 16; ++kk) {
-                            const uint32_t acc = (first && kk == 0) ? 0u : 1u;
-                            const uint64_t a0 = dbase + (uint64_t)((kk * 32) >> 4);
-                            const uint64_t a1 = dbase + (uint64_t)((TILE_BYTES + kk * 32) >> 4);
-                            const uint64_t b0 = dbase + (uint64_t)((S * TILE_BYTES + kk * 32) >> 4);
-                            const uint64_t b1 = dbase + (uint64_t)((S * TILE_BYTES + B_TILE + kk * 32) >> 4);
-                            if constexpr (CG == 1) {
-                                // B0 and B1 are adjacent 128-row tiles, ACC0 and ACC01
-                                // adjacent TMEM columns: one N = 256 product makes both
-                                mma_bf16<CG>(acc0, a0, b0, IDESC_N256, acc);
-                            } else {
-                                mma_bf16<CG>(acc0, a0, b0, IDESC, acc);
-                                mma_bf16<CG>(acc01, a0, b1, IDESC, acc);
-                            }
-                            mma_bf16<CG>(acc10, a1, b0, IDESC, acc);
-                        }
-                    };
-                    // the rest (2 <= p + q < S), into ACCR over the whole tile
-                    auto issue_rest = [&]() {
+                    // the instructions of one group for both 16-wide K steps
+                    auto issue = [&](int group) {
 #pragma unroll
                         for (int kk = 0; kk < BK / 16; ++kk) {
 #pragma unroll
-                            for (int p = 0; p < S; ++p) {
-#pragma unroll
-                                for (int q = 0; q + p < S; ++q) {
-                                    if (p + q < 2) continue;
-                                    const uint64_t da = dbase + (uint64_t)((p * TILE_BYTES + kk * 32) >> 4);
-                                    const uint64_t db = dbase + (uint64_t)((S * TILE_BYTES + q * B_TILE + kk * 32) >> 4);
-                                    mma_bf16<CG>(accr, da, db, IDESC, accr_started ? 1u : 0u);
-                                    accr_started = true;
+                            for (int t = 0; t < ins_count(S); ++t) {
+                                const SliceIns in = ins_of(S, t);
+                                if (in.group != group) continue;
+                                uint32_t acc = 1u;
+                                if (in.flag == 0) acc = (chunk_start && kk == 0) ? 0u : 1u;
+                                if (in.flag == 1) acc = (kb == 0 && kk == 0) ? 0u : 1u;
+                                const uint64_t da = dbase + (uint64_t)((in.a * TILE_BYTES + kk * 32) >> 4);
+                                const uint64_t db = dbase + (uint64_t)((S * TILE_BYTES + in.b * B_TILE + kk * 32) >> 4);
+                                if constexpr (CG == 1) {
+                                    // B_q and B_q+1 are adjacent 128-row tiles: one N = 256 product
+                                    mma_bf16<CG>(tmem + in.col, da, db, in.wide ? IDESC_N256 : IDESC, acc);
+                                } else {
+                                    // a pair stages half of each B tile: two N = 128 products, same order
+                                    mma_bf16<CG>(tmem + in.col, da, db, IDESC, acc);
+                                    if (in.wide)
+                                        mma_bf16<CG>(tmem + in.col + 128, da, db + (uint64_t)(B_TILE >> 4), IDESC, acc);
                                 }
                             }
                         }
                     };
                     if (chunk_start && kb > 0) {
                         // a drain of the exact accumulators inside this tile is
-                        // pending: keep the tensor pipe busy on ACCR meanwhile
-                        issue_rest();
+                        // pending: keep the tensor pipe busy on R / R2 meanwhile
+                        issue(2);
                         ok = mbar_wait(acc_empty, (chunk_no - 1) & 1, abort_flag, g.status);
                         if (!ok) break;
                         tc_fence_after();
-                        issue_exact(true);
+                        issue(1);
                     } else {
                         if (chunk_start && chunk_no > 0) {
-                            // the previous tile's results (ACCR included) have been read
+                            // the previous tile's results (R and R2 included) have been read
                             ok = mbar_wait(acc_empty, (chunk_no - 1) & 1, abort_flag, g.status);
                             if (!ok) break;
                             tc_fence_after();
                         }
-                        issue_exact(chunk_start);
+                        issue(1);
                         if (chunk_end && !tile_end) {
-                            mma_commit_all<CG>(acc_full);    // tracks the exact products only
+                            mma_commit_all<CG>(acc_full);    // tracks group 1 (ACC0, ACC1) only
                             ++chunk_no;
                         }
-                        issue_rest();
+                        issue(2);
                     }
                     mma_commit_all<CG>(&empty[stage]);
                     if (tile_end) {
@@ -498,11 +559,12 @@ k_split_mma(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
         uint32_t chunk_no = 0;
         bool ok = true;
         for (int tile = first_tile; tile < num_tiles && ok; tile += tile_step) {
-            const int mb = tile / tiles_n, nb = tile % tiles_n;
+            int mb, nb;
+            tile_coords(tile, tiles_m, tiles_n, g.group_n, mb, nb);
             const int row0 = mb * TILE_M + (int)rank * BM;   // this CTA's rows of the tile
-            // J = I0 2^8 + I1: the exact ACC0 and ACC01 + ACC10 sums of this
-            // tile's columns in one int64 each; at the end J becomes
-            // V = J 2^14 + rint(ACCR 2^22) and then, in place, the FP64 bits
+            // J = I0 2^8 + I1: the exact ACC0 and ACC1 sums of this tile's
+            // columns in one int64 each; at the end J becomes
+            // V = J 2^14 + rint(R 2^22) + rint(R2 2^22) and then, in place, the FP64 bits
             long long J[CPT];
 #pragma unroll
             for (int j = 0; j < CPT; ++j) J[j] = 0;
@@ -529,23 +591,27 @@ k_split_mma(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
                     tmem_wait_ld();
 #pragma unroll
                     for (int j = 0; j < 8; ++j) J[h * 8 + j] += __float2int_rn(__uint_as_float(r[j]) * 256.0f);
-                    tmem_ld8(tmem + lane_base + 256 + col, r);
-                    tmem_wait_ld();
-#pragma unroll
-                    for (int j = 0; j < 8; ++j) J[h * 8 + j] += __float2int_rn(__uint_as_float(r[j]) * 256.0f);
                     if (last) {
-                        // fold in ACCR: J becomes V = J 2^14 + rint(ACCR 2^22)
+                        // fold in R and R2: J becomes V = J 2^14 + rint(R 2^22) + rint(R2 2^22)
+                        // (with two slices no product lands in R, with three none in R2:
+                        // their columns are never written and read as zero here)
+                        long long rr[8];
+#pragma unroll
+                        for (int j = 0; j < 8; ++j) rr[j] = 0;
                         if (S >= 3) {
+                            tmem_ld8(tmem + lane_base + 256 + col, r);
+                            tmem_wait_ld();
+#pragma unroll
+                            for (int j = 0; j < 8; ++j) rr[j] = rint_f32_to_i64(__uint_as_float(r[j]) * 4194304.0f);
+                        }
+                        if (S >= 4) {
                             tmem_ld8(tmem + lane_base + 384 + col, r);
                             tmem_wait_ld();
-                        } else {
-                            // two slices: no product lands in ACCR, whose columns are never written
 #pragma unroll
-                            for (int j = 0; j < 8; ++j) r[j] = 0u;
+                            for (int j = 0; j < 8; ++j) rr[j] += rint_f32_to_i64(__uint_as_float(r[j]) * 4194304.0f);
                         }
 #pragma unroll
-                        for (int j = 0; j < 8; ++j)
-                            J[h * 8 + j] = (J[h * 8 + j] << 14) + rint_f32_to_i64(__uint_as_float(r[j]) * 4194304.0f);
+                        for (int j = 0; j < 8; ++j) J[h * 8 + j] = (J[h * 8 + j] << 14) + rr[j];
                     }
                 }
                 // TMEM is free for the next tile before the FP64 results are
@@ -750,8 +816,33 @@ CUtensorMap make_map(const void* base, int rows, int kp, int box_rows = BM) {
     return m;
 }
 
+// Column blocks per tile group.  The CTAs of a wave walk K in near lockstep,
+// so a row block of A is read once by the group_n CTAs that share it and
+// then streams on; the column blocks of B are re-read by every wave of the
+// group and stay in L2 only if group_n of them fit.  Pick the group width
+// with the fewest operand bytes read from DRAM under that model.
+int choose_group_n(int tiles_m, int tiles_n, int grid, int kp, int S) {
+    const double block = (double)BM * kp * S * 2;            // bytes of one 128-row slice block
+    const double budget = 80.0 * (1 << 20);
+    int best = tiles_n;
+    double best_cost = 1e300;
+    int prev = -1;
+    for (int parts = 1; parts <= tiles_n; ++parts) {
+        const int g = (tiles_n + parts - 1) / parts;
+        if (g == prev) continue;
+        prev = g;
+        const int groups = (tiles_n + g - 1) / g;
+        const double waves_per_group = std::ceil((double)tiles_m * g / grid);
+        const double b_reads = (g * block <= budget) ? 1.0 : waves_per_group;
+        const double cost = groups * tiles_m * block + b_reads * tiles_n * block;
+        if (cost < best_cost) { best_cost = cost; best = g; }
+    }
+    return std::max(1, best);
+}
+
 template <int S, int CG>
-void launch_mma(Ctx& ctx, const CUtensorMap& ta, const CUtensorMap& tb, const MmaArgs& a) {
+void launch_mma(Ctx& ctx, const CUtensorMap& ta, const CUtensorMap& tb, const MmaArgs& a0) {
+    MmaArgs a = a0;
     static std::once_flag once;
     static int max_clusters = 0;
     std::call_once(once, [&ctx] {
@@ -771,10 +862,13 @@ void launch_mma(Ctx& ctx, const CUtensorMap& ta, const CUtensorMap& tb, const Mm
             TRG_CUDA(cudaOccupancyMaxActiveClusters(&max_clusters, k_split_mma<S, CG>, &cfg));
         }
     });
-    const int tiles = ((a.M + BM * CG - 1) / (BM * CG)) * ((a.N + BN - 1) / BN);
+    const int tiles_m = (a.M + BM * CG - 1) / (BM * CG), tiles_n = (a.N + BN - 1) / BN;
+    const int tiles = tiles_m * tiles_n;
+    const int ctas = CG == 1 ? std::max(1, std::min(tiles, ctx.sm_count)) : 2 * std::max(1, std::min(tiles, max_clusters));
+    a.group_n = choose_group_n(tiles_m * CG, tiles_n, ctas, a.Kp, S);
     cudaError_t e;
     if (CG == 1) {
-        const int grid = std::max(1, std::min(tiles, ctx.sm_count));
+        const int grid = ctas;
         k_split_mma<S, CG><<<grid, THREADS, smem_bytes_for(S, CG), ctx.stream>>>(ta, tb, a);
         e = cudaGetLastError();
     } else {
@@ -1029,6 +1123,7 @@ extern "C" int trg_gemm_noalloc(int M, int N, int K, const double* A, int lda, c
         a.cons_ef = nullptr; a.cons_m = nullptr; a.cons_n = nullptr;
         const int tiles = ((M + BM - 1) / BM) * ((N + BN - 1) / BN);
         const int grid = std::max(1, std::min(tiles, sms));
+        a.group_n = choose_group_n((M + BM - 1) / BM, (N + BN - 1) / BN, grid, Kp, S);
         switch (S) {
 #define TRG_NOALLOC_MMA(SS)                                                                                  \
     TRG_CUDA(cudaFuncSetAttribute(k_split_mma<SS, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,           \
