@@ -40,6 +40,8 @@ def parse():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--precision", default=None, choices=["split", "fp64"])
     ap.add_argument("--slices", type=int, default=4)
+    ap.add_argument("--fused-slices", type=int, default=1, choices=[0, 1, 2],
+                    help="slice hand-over between contraction products: none (0), D^7 -> last (1), all (2)")
     ap.add_argument("--mma-pairs", type=int, default=0, choices=[0, 1],
                     help="split products on CTA pairs (1) or one CTA per tile (0)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -197,7 +199,8 @@ def run_native(args):
         torch.cuda.synchronize()
 
     stream = torch.cuda.current_stream()
-    s = Solver(local, stream=stream, precision=precision, split_slices=args.slices, mma_pairs=args.mma_pairs)
+    s = Solver(local, stream=stream, precision=precision, split_slices=args.slices, mma_pairs=args.mma_pairs,
+               fused_slices=args.fused_slices)
     # replicas: every rank solves its own coupling (beta_c shifted per rank)
     beta = BETA_C * (1.0 + 1e-4 * rank)
     s.init_tensor("ising", beta, 0.0)

@@ -82,6 +82,12 @@ typedef struct trg_config {
                                 CTA pairs (256-row tiles, cta_group::2, each CTA staging
                                 half of B); 0 (default) keeps one CTA per 128 x 128 tile.
                                 Results are identical either way. */
+    int fused_slices;        /* TRG_SPLIT_BF16, bond dimensions 32, 64 or 128: 1 (default)
+                                lets the D^7 contraction product write the last product's
+                                BF16 operand slices directly (no FP64 intermediate, no
+                                slicing pass); 2 also hands the first product over as
+                                slices; 0 always goes through FP64.  Results are identical
+                                in all three. */
 } trg_config;
 
 typedef struct trg_ctx trg_ctx;

@@ -40,6 +40,7 @@ class trg_config(ctypes.Structure):
         ("seed", c_uint64),
         ("workspace_bytes", c_size_t),
         ("mma_pairs", c_int),
+        ("fused_slices", c_int),
     ]
 
 

@@ -240,6 +240,7 @@ int trg_config_default(trg_config* cfg) {
     cfg->seed = 0x5EEDull;
     cfg->workspace_bytes = 0;
     cfg->mma_pairs = 0;
+    cfg->fused_slices = 1;
     return TRG_OK;
 }
 
@@ -248,6 +249,7 @@ static int validate_config(const trg_config& c) {
     if (c.split_slices < 2 || c.split_slices > 5) return TRG_EINVAL;
     if (c.split_from_step < 0) return TRG_EINVAL;
     if (c.mma_pairs != 0 && c.mma_pairs != 1) return TRG_EINVAL;
+    if (c.fused_slices < 0 || c.fused_slices > 2) return TRG_EINVAL;
     if (c.trunc != TRG_TRUNC_PAPER && c.trunc != TRG_TRUNC_MULTIPLET) return TRG_EINVAL;
     if (!(c.gap_tol >= 0.0) || !(c.eig_tol > 0.0) || c.oversample < 1 || c.eig_max_iter < 1) return TRG_EINVAL;
     return TRG_OK;

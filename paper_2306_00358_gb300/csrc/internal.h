@@ -138,6 +138,11 @@ struct GemmDesc {
     const int64_t* c_m;
     const int64_t* c_n;
     double beta = 0.0;      // 0: overwrite, 1: accumulate
+    // The split epilogue may store without staging when consecutive rows are
+    // adjacent in C and c_n[n + j] = c_n[n] + j c_col_stride inside each
+    // aligned group of 32 columns.
+    bool c_rows_fast = false;
+    int64_t c_col_stride = 0;
     // Split mode only.  Producer side: record, for the product that will
     // consume C as its A operand, the largest FP64 exponent field of each of
     // its rows (row of element (m, n) = cons_m[m] + cons_n[n]) into cons_ef
@@ -147,7 +152,27 @@ struct GemmDesc {
     const int64_t* cons_m = nullptr;
     const int64_t* cons_n = nullptr;
     const int* a_ef = nullptr;
+    // Split mode, fused hand-over: instead of C, the producer writes the
+    // consumer's BF16 A slices ([S][Mp][Kp], element (m, n) at consumer row
+    // cons_m[m] + cons_n[n], column ck_m[m] + ck_n[n]) and their row
+    // exponents (cs_e).  Valid when every consumer row lies in one 128 x 128
+    // tile as rows_per_crow consecutive rows (a multiple of 32) times
+    // cols_per_crow consecutive columns (32, 64 or 128); the consumer then
+    // takes a_slices / a_e and skips slicing A.  Bit-identical to slicing C.
+    uint16_t* cs_out = nullptr;
+    int64_t cs_mp = 0, cs_kp = 0;
+    int* cs_e = nullptr;
+    const int64_t* ck_m = nullptr;
+    const int64_t* ck_n = nullptr;
+    int rows_per_crow = 0, cols_per_crow = 0;
+    int64_t ck_stride = 0;  // consumer column of producer column n + 1 minus that of n, inside a row group
+    const uint16_t* a_slices = nullptr;
+    const int* a_e = nullptr;
 };
+// Rows and columns of the padded slice arrays a split product of M rows and
+// K columns reads for its A operand (the fused hand-over writes this layout).
+int64_t split_rows_padded(const Ctx& ctx, int64_t M);
+int64_t split_k_padded(int64_t K);
 void gemm(Ctx& ctx, const GemmDesc& g, int precision);
 void gemm_f64(Ctx& ctx, const GemmDesc& g);
 

@@ -121,25 +121,46 @@ void environment(Ctx& ctx, const View4& t, double* M, int precision) {
 }
 
 // Tx[i,j,k,l] = sum U[a,b,i] t[b,j,d,c] t[a,c,e,l] U[e,d,k], in slices of j:
-//   X1[(jj,i,d),(a,c)] = sum_b U[a,b,i] t[b,j0+jj,d,c]          (D^6)
-//   X2[(jj,i,l),(d,e)] = sum_{a,c} X1[(jj,i,d),(a,c)] t[a,c,e,l]  (D^7; columns of the
-//                        product ordered (l,e), stored so the next product reads (d,e) rows)
-//   O[i,j0+jj,k,l]     = sum_{d,e} X2[(jj,i,l),(d,e)] U[e,d,k]    (D^6)
-// In split mode each producer records the exponent fields of its consumer's
-// rows, so the consumer skips the exponent pass over the D^5 slice.
+//   X1[(jj,i,d),(c,a)] = sum_b U[a,b,i] t[b,j0+jj,d,c]          (D^6)
+//   X2[(jj,i,l),(e,d)] = sum_{c,a} X1[(jj,i,d),(c,a)] t[a,c,e,l]  (D^7)
+//   O[i,j0+jj,k,l]     = sum_{e,d} X2[(jj,i,l),(e,d)] U[e,d,k]    (D^6)
+// The summed pair of each product is ordered with the producer's row index
+// fastest ((c,a) and (e,d)), so a producer warp, whose lanes are adjacent
+// rows, writes adjacent elements of its consumer's rows.  In split mode each
+// producer either records the exponent fields of its consumer's rows (the
+// consumer then skips the exponent pass over the D^5 intermediate) or, when
+// the bond dimensions tile (32, 64, 128), writes the consumer's slices.
 void contract(Ctx& ctx, const View4& t, const double* U, int64_t Dn, const View4& out, int precision) {
     const int64_t Dx = t.n[0], Dy = t.n[1];
     const int64_t* s = t.s;
     const int64_t* o = out.s;
     const int64_t DD = Dx * Dy;
-    const size_t ws_cap = ctx.cfg.workspace_bytes ? ctx.cfg.workspace_bytes : ((size_t)4 << 30);
-    const size_t per_j = (size_t)(2 * Dn * Dx * DD) * sizeof(double);
-    int64_t jb = std::max<int64_t>(1, std::min<int64_t>(Dy, (int64_t)(ws_cap / per_j)));
-    ctx.ensure(ctx.ws, per_j * (size_t)jb);
-    double* X1 = ctx.ws.as<double>();
-    double* X2 = X1 + jb * Dn * Dx * DD;
     const bool split = precision == TRG_SPLIT_BF16;
+    // Fused hand-over (split mode): when a consumer row of the next product is
+    // Dx x Dx elements of one 128 x 128 output tile, the producer writes the
+    // next product's A slices directly (bit-identical to slicing its FP64
+    // output).  Done for X2 -> O: the D^7 product is tensor-bound, so the
+    // heavier epilogue hides behind its MMAs and the slicing pass over X2
+    // disappears.  X1 (K = Dx) is bound by its epilogue already; it keeps the
+    // FP64 hand-over, whose epilogue is half as long as the slicing one.
+    // fused_slices = 2 hands X1 over as slices too (same results, slower here).
+    auto tiles_ok = [](int64_t v) { return v == 32 || v == 64 || v == 128; };
+    const bool fuse = split && ctx.cfg.fused_slices >= 1 && tiles_ok(Dx);
+    const bool fuse1 = split && ctx.cfg.fused_slices == 2 && tiles_ok(Dx) && tiles_ok(Dy);
+    const int S = ctx.cfg.split_slices;
+    const size_t ws_cap = ctx.cfg.workspace_bytes ? ctx.cfg.workspace_bytes : ((size_t)4 << 30);
+    // bytes per j of each intermediate: FP64, or S BF16 slices (+ padding rows)
+    const size_t elem = (fuse || fuse1) ? (size_t)std::max(8, 2 * S) : 8;
+    const size_t per_j = (size_t)(2 * Dn * Dx * DD) * elem;
+    int64_t jb = std::max<int64_t>(1, std::min<int64_t>(Dy, (int64_t)(ws_cap / per_j)));
     const int64_t rows2 = jb * Dn * Dx, rows3 = jb * Dn * Dy;   // A rows of the two consumers
+    size_t r1 = (size_t)(rows2 * DD) * 8, r2 = (size_t)(rows3 * Dx * Dx) * 8;
+    if (fuse1) r1 = std::max(r1, (size_t)S * split_rows_padded(ctx, rows2) * split_k_padded(DD) * 2);
+    if (fuse) r2 = std::max(r2, (size_t)S * split_rows_padded(ctx, rows3) * split_k_padded(Dx * Dx) * 2);
+    r1 = (r1 + 255) & ~(size_t)255;
+    ctx.ensure(ctx.ws, r1 + r2);
+    double* X1 = ctx.ws.as<double>();
+    double* X2 = (double*)(ctx.ws.as<uint8_t>() + r1);
     int* ef2 = nullptr;
     int* ef3 = nullptr;
     if (split) {
@@ -150,53 +171,100 @@ void contract(Ctx& ctx, const View4& t, const double* U, int64_t Dn, const View4
 
     for (int64_t j0 = 0; j0 < Dy; j0 += jb) {
         const int64_t jn = std::min(jb, Dy - j0);
-        {   // X1
+        const int64_t M2 = jn * Dn * Dx, M3 = jn * Dn * Dy;       // rows of this block's X2 / O products
+        {   // X1[(jj,i,d),(c,a)] = sum_b U[a,b,i] t[b,j0+jj,d,c]: rows (i,a), a fastest,
+            // so a warp's lanes hold adjacent a (adjacent in X1, one consumer row)
             ctx.phase = TRG_PHASE_X1;
             GemmDesc g;
             g.M = Dx * Dn; g.N = jn * DD; g.K = Dx;
-            g.A = gather(ctx, U, {{Dx, Dx * Dn}, {Dn, 1}}, {{Dx, Dn}});
+            g.A = gather(ctx, U, {{Dn, 1}, {Dx, Dx * Dn}}, {{Dx, Dn}});
             g.B = gather(ctx, t.p + j0 * s[1], {{Dx, s[0]}}, {{jb, s[1]}, {Dx, s[2]}, {Dy, s[3]}});
-            g.C = X1;
-            g.c_m = ctx.table({{Dx, Dy}, {Dn, Dx * DD}});
-            g.c_n = ctx.table({{jb, Dn * Dx * DD}, {Dx, DD}, {Dy, 1}});
-            if (split) {
-                // consumer row of element ((a,i),(jj,d,c)) is (jj,i,d)
-                TRG_CUDA(cudaMemsetAsync(ef2, 0, (size_t)rows2 * sizeof(int), ctx.stream));
-                g.cons_ef = ef2;
-                g.cons_m = ctx.table({{Dx, 0}, {Dn, Dx}});
-                g.cons_n = ctx.table({{jb, Dn * Dx}, {Dx, 1}, {Dy, 0}});
+            // consumer row of element ((i,a),(jj,d,c)) is (jj,i,d), its column c Dx + a
+            g.cons_m = ctx.table({{Dn, Dx}, {Dx, 0}});
+            g.cons_n = ctx.table({{jb, Dn * Dx}, {Dx, 1}, {Dy, 0}});
+            if (fuse1) {
+                g.C = nullptr;
+                g.cs_out = (uint16_t*)X1;
+                g.cs_mp = split_rows_padded(ctx, M2);
+                g.cs_kp = split_k_padded(DD);
+                g.cs_e = ef2;
+                g.ck_m = ctx.table({{Dn, 0}, {Dx, 1}});
+                g.ck_n = ctx.table({{jb, 0}, {Dx, 0}, {Dy, Dx}});
+                g.ck_stride = Dx;
+                g.rows_per_crow = (int)Dx;
+                g.cols_per_crow = (int)Dy;
+            } else {
+                g.C = X1;
+                g.c_m = ctx.table({{Dn, Dx * DD}, {Dx, 1}});
+                g.c_n = ctx.table({{jb, Dn * Dx * DD}, {Dx, DD}, {Dy, Dx}});
+                g.c_rows_fast = Dy % 32 == 0;
+                g.c_col_stride = Dx;
+                if (split) {
+                    TRG_CUDA(cudaMemsetAsync(ef2, 0, (size_t)rows2 * sizeof(int), ctx.stream));
+                    g.cons_ef = ef2;
+                } else {
+                    g.cons_m = g.cons_n = nullptr;
+                }
             }
             gemm(ctx, g, precision);
         }
-        {   // X2 (the D^7 product)
+        {   // X2[(jj,i,l),(e,d)] = sum_{c,a} X1[(jj,i,d),(c,a)] t[a,c,e,l]  (the D^7 product):
+            // rows (jj,i,d), d fastest; columns (l,e), e fastest
             ctx.phase = TRG_PHASE_X2;
             GemmDesc g;
-            g.M = jn * Dn * Dx; g.N = DD; g.K = DD;
+            g.M = M2; g.N = DD; g.K = DD;
             g.A = gather(ctx, X1, {{jb * Dn * Dx, DD}}, {{DD, 1}});
-            g.B = gather(ctx, t.p, {{Dx, s[0]}, {Dy, s[1]}}, {{Dy, s[3]}, {Dx, s[2]}});
-            g.C = X2;
-            g.c_m = ctx.table({{jb * Dn, Dy * Dx * Dx}, {Dx, Dx}});
-            g.c_n = ctx.table({{Dy, Dx * Dx}, {Dx, 1}});
-            if (split) {
+            g.B = gather(ctx, t.p, {{Dy, s[1]}, {Dx, s[0]}}, {{Dy, s[3]}, {Dx, s[2]}});
+            // consumer row of element ((jj,i,d),(l,e)) is (jj,i,l), its column e Dx + d
+            g.cons_m = ctx.table({{jb * Dn, Dy}, {Dx, 0}});
+            g.cons_n = ctx.table({{Dy, 1}, {Dx, 0}});
+            if (fuse1) {
+                g.a_slices = (const uint16_t*)X1;
+                g.a_e = ef2;
+            } else if (split) {
                 g.a_ef = ef2;
-                // consumer row of element ((jj,i,d),(l,e)) is (jj,i,l)
-                TRG_CUDA(cudaMemsetAsync(ef3, 0, (size_t)rows3 * sizeof(int), ctx.stream));
-                g.cons_ef = ef3;
-                g.cons_m = ctx.table({{jb * Dn, Dy}, {Dx, 0}});
-                g.cons_n = ctx.table({{Dy, 1}, {Dx, 0}});
+            }
+            if (fuse) {
+                g.C = nullptr;
+                g.cs_out = (uint16_t*)X2;
+                g.cs_mp = split_rows_padded(ctx, M3);
+                g.cs_kp = split_k_padded(Dx * Dx);
+                g.cs_e = ef3;
+                g.ck_m = ctx.table({{jb * Dn, 0}, {Dx, 1}});
+                g.ck_n = ctx.table({{Dy, 0}, {Dx, Dx}});
+                g.ck_stride = Dx;
+                g.rows_per_crow = (int)Dx;
+                g.cols_per_crow = (int)Dx;
+            } else {
+                g.C = X2;
+                g.c_m = ctx.table({{jb * Dn, Dy * Dx * Dx}, {Dx, 1}});
+                g.c_n = ctx.table({{Dy, Dx * Dx}, {Dx, Dx}});
+                g.c_rows_fast = Dx % 32 == 0;
+                g.c_col_stride = Dx;
+                if (split) {
+                    TRG_CUDA(cudaMemsetAsync(ef3, 0, (size_t)rows3 * sizeof(int), ctx.stream));
+                    g.cons_ef = ef3;
+                } else {
+                    g.cons_m = g.cons_n = nullptr;
+                }
             }
             gemm(ctx, g, precision);
         }
-        {   // O
+        {   // O[i,j0+jj,k,l] = sum_{e,d} X2[(jj,i,l),(e,d)] U[e,d,k]
             ctx.phase = TRG_PHASE_X3;
             GemmDesc g;
-            g.M = jn * Dn * Dy; g.N = Dn; g.K = Dx * Dx;
+            g.M = M3; g.N = Dn; g.K = Dx * Dx;
             g.A = gather(ctx, X2, {{jb * Dn * Dy, Dx * Dx}}, {{Dx * Dx, 1}});
-            g.B = gather(ctx, U, {{Dx, Dn}, {Dx, Dx * Dn}}, {{Dn, 1}});
+            g.B = gather(ctx, U, {{Dx, Dx * Dn}, {Dx, Dn}}, {{Dn, 1}});
             g.C = out.p + j0 * o[1];
             g.c_m = ctx.table({{jb, o[1]}, {Dn, o[0]}, {Dy, o[3]}});
             g.c_n = ctx.table({{Dn, o[2]}});
-            if (split) g.a_ef = ef3;
+            if (fuse) {
+                g.a_slices = (const uint16_t*)X2;
+                g.a_e = ef3;
+            } else if (split) {
+                g.a_ef = ef3;
+            }
             gemm(ctx, g, precision);
         }
     }

@@ -66,6 +66,7 @@ constexpr unsigned long long WAIT_NS = 2000000000ull;   // bounded mbarrier wait
 constexpr int CPT = 32;                        // accumulator columns per epilogue thread
 constexpr int STAGING_BYTES = EPI_WARPS * 32 * 8 * 8;    // epilogue store staging, 32 KB
 constexpr int SMEM_LIMIT = 232448;             // opt-in shared memory per block
+constexpr int BAR_BYTES = 512;                 // mbarriers, TMEM address, flags, row maxima
 
 // CG = CTAs per MMA (1, or a pair with cta_group::2).  A CTA stages its own
 // 128 rows of A and 128 / CG columns of B per slice and stage.
@@ -73,14 +74,14 @@ __host__ __device__ constexpr int b_tile_bytes(int CG) { return TILE_BYTES / CG;
 __host__ __device__ constexpr int stage_bytes_for(int S, int CG) { return S * (TILE_BYTES + b_tile_bytes(CG)); }
 __host__ __device__ constexpr int stages_for(int S, int CG) {
     return CG == 1 ? (S <= 4 ? 3 : 2)
-                   : ((SMEM_LIMIT - 1024 - 256 - STAGING_BYTES) / stage_bytes_for(S, CG) > 6
+                   : ((SMEM_LIMIT - 1024 - BAR_BYTES - STAGING_BYTES) / stage_bytes_for(S, CG) > 6
                           ? 6
-                          : (SMEM_LIMIT - 1024 - 256 - STAGING_BYTES) / stage_bytes_for(S, CG));
+                          : (SMEM_LIMIT - 1024 - BAR_BYTES - STAGING_BYTES) / stage_bytes_for(S, CG));
 }
 __host__ __device__ constexpr int smem_bytes_for(int S, int CG) {
     // at least 120 KB so that a second CTA (and its 512 TMEM columns) never shares the SM
-    return (stages_for(S, CG) * stage_bytes_for(S, CG) + 1024 + 256 + STAGING_BYTES) > 120 * 1024
-               ? stages_for(S, CG) * stage_bytes_for(S, CG) + 1024 /*align*/ + 256 /*barriers*/ + STAGING_BYTES
+    return (stages_for(S, CG) * stage_bytes_for(S, CG) + 1024 + BAR_BYTES + STAGING_BYTES) > 120 * 1024
+               ? stages_for(S, CG) * stage_bytes_for(S, CG) + 1024 /*align*/ + BAR_BYTES + STAGING_BYTES
                : 120 * 1024;
 }
 static_assert(smem_bytes_for(2, 2) <= SMEM_LIMIT && smem_bytes_for(3, 2) <= SMEM_LIMIT &&
@@ -272,6 +273,66 @@ __device__ __forceinline__ double scaled_i64_to_double(long long v, int e2) {
     return __longlong_as_double((long long)bits);
 }
 
+// |v| rounded to 53 significant bits (half to even), as the FP64 value of v
+// has it, and the position of its leading one afterwards.
+__device__ __forceinline__ unsigned long long round53(unsigned long long a, int& top) {
+    top = 63 - __clzll((long long)a);
+    if (top <= 52) return a;
+    const int sh = top - 52;
+    const unsigned long long half = 1ull << (sh - 1);
+    const unsigned long long rem = a & ((1ull << sh) - 1);
+    unsigned long long mant = a >> sh;
+    if (rem > half || (rem == half && (mant & 1))) {
+        ++mant;
+        if (mant >> 53) { mant >>= 1; ++top; }
+    }
+    return mant << (top - 52);
+}
+// Biased exponent field of the FP64 value v 2^e2 (0 when v = 0 or the value
+// flushes to zero, as in scaled_i64_to_double).
+__device__ __forceinline__ int fp64_exponent_field(long long v, int e2) {
+    if (v == 0) return 0;
+    int top;
+    round53(v < 0 ? (unsigned long long)(-v) : (unsigned long long)v, top);
+    const int ex = top + e2 + 1023;
+    return ex < 1 ? 0 : (ex > 2046 ? 2047 : ex);
+}
+// The fixed-point integer X = rint(x 2^(F - e_row)) (halves away from zero)
+// that slicing the FP64 value x = v 2^e2 produces, computed from v: with
+// V53 = |v| rounded to 53 bits and r = e_row - e2 - F, X = V53 / 2^r rounded
+// (r > 0) or V53 2^-r (r <= 0).
+// The same two for |v| < 2^53, where the FP64 value holds v exactly.
+__device__ __forceinline__ int fp64_exponent_field_exact(long long v, int e2) {
+    if (v == 0) return 0;
+    const int top = 63 - __clzll(v < 0 ? -v : v);
+    const int ex = top + e2 + 1023;
+    return ex < 1 ? 0 : (ex > 2046 ? 2047 : ex);
+}
+template <int S>
+__device__ __forceinline__ long long fused_fixed_point_exact(long long v, int e2, int e_row) {
+    constexpr int F = 7 + 8 * (S - 1);
+    if (v == 0) return 0;
+    const unsigned long long a = (unsigned long long)(v < 0 ? -v : v);
+    if (63 - __clzll((long long)a) + e2 + 1023 < 1) return 0;   // the FP64 value flushes to zero
+    const int r = e_row - e2 - F;
+    const long long X = r >= 63 ? 0 : r > 0 ? (long long)((a + (1ull << (r - 1))) >> r) : (long long)(a << (-r));
+    return v < 0 ? -X : X;
+}
+template <int S>
+__device__ __forceinline__ long long fused_fixed_point(long long v, int e2, int e_row) {
+    constexpr int F = 7 + 8 * (S - 1);
+    if (v == 0) return 0;
+    int top;
+    const unsigned long long a = round53(v < 0 ? (unsigned long long)(-v) : (unsigned long long)v, top);
+    if (top + e2 + 1023 < 1) return 0;           // the FP64 value flushes to zero
+    const int r = e_row - e2 - F;
+    long long X;
+    if (r >= 63) X = 0;
+    else if (r > 0) X = (long long)((a + (1ull << (r - 1))) >> r);
+    else X = (long long)(a << (-r));
+    return v < 0 ? -X : X;
+}
+
 struct MmaArgs {
     int M, N, Kp;                  // logical rows / cols, padded K (multiple of BK)
     int Mp, Np;                    // padded rows of the A / B slice arrays
@@ -286,6 +347,18 @@ struct MmaArgs {
     const int64_t* cons_m;
     const int64_t* cons_n;
     int group_n;               // tile order: column blocks per group (see tile_coords)
+    // optional fused hand-over: the consumer's A slices instead of C
+    uint16_t* cs_out;
+    int64_t cs_plane;          // Mp * Kp of the consumer's slice arrays
+    int64_t cs_kp;
+    int* cs_e;
+    const int64_t* ck_m;
+    const int64_t* ck_n;
+    int rows_per_crow, cols_per_crow;
+    int64_t ck_stride;         // fused: consumer-column step between adjacent producer columns
+    int v_exact53;             // fused: every V is below 2^53 in magnitude (K <= 8192)
+    int c_rows_fast;           // C's rows are adjacent: store without staging ...
+    int64_t c_col_stride;      // ... with c_n[n + j] = c_n[n] + j c_col_stride in a 32-column group
 };
 
 // Tile order: column blocks in groups of group_n; inside a group the tiles run
@@ -360,7 +433,13 @@ __host__ __device__ constexpr bool ins_cover_ok(int S) {
 }
 static_assert(ins_cover_ok(2) && ins_cover_ok(3) && ins_cover_ok(4) && ins_cover_ok(5), "slice product table");
 
-template <int S, int CG>
+// Epilogue kinds: FP64 results stored through a staging tile (columns
+// adjacent in C), stored directly (rows adjacent in C), or the consumer's
+// slices (fused hand-over).  One kernel instance each keeps the register
+// allocation of each epilogue to itself.
+enum EpiMode { EPI_STAGED = 0, EPI_DIRECT = 1, EPI_FUSED = 2 };
+
+template <int S, int CG, int MODE>
 __global__ void __launch_bounds__(THREADS, 1)
 k_split_mma(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, const MmaArgs g) {
     constexpr int STAGES = stages_for(S, CG);
@@ -375,9 +454,11 @@ k_split_mma(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
     uint64_t* acc_full = empty + STAGES;
     uint64_t* acc_empty = acc_full + 1;
     uint64_t* mma_done = acc_empty + 1;
-    uint32_t* tmem_slot = (uint32_t*)(mma_done + 1);
+    uint64_t* cs_bar = mma_done + 1;             // epilogue warps: consumer-row maxima are complete
+    uint32_t* tmem_slot = (uint32_t*)(cs_bar + 1);
     volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
-    double* staging = (double*)(smem + STAGES * STAGE_BYTES + 256);   // EPI_WARPS x 32 x 8 doubles
+    unsigned* cs_slot = (unsigned*)(tmem_slot + 4);   // 2 x 16 consumer-row maxima, tagged by tile
+    double* staging = (double*)(smem + STAGES * STAGE_BYTES + BAR_BYTES);   // EPI_WARPS x 32 x 8 doubles
 
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
@@ -395,7 +476,9 @@ k_split_mma(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
         mbar_init(acc_full, 1);
         mbar_init(acc_empty, EPI_WARPS * CG);
         mbar_init(mma_done, 1);
+        mbar_init(cs_bar, EPI_WARPS);
         *abort_flag = 0;
+        for (int i = 0; i < 32; ++i) cs_slot[i] = 0u;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
@@ -557,10 +640,12 @@ k_split_mma(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
         const int row_in_tile = quad * 32 + lane;
         const int nchunks = (num_kb + CHUNK_STAGES - 1) / CHUNK_STAGES;
         uint32_t chunk_no = 0;
+        uint32_t tile_iter = 0;                   // tiles done by this CTA (tags the row maxima)
         bool ok = true;
         for (int tile = first_tile; tile < num_tiles && ok; tile += tile_step) {
             int mb, nb;
             tile_coords(tile, tiles_m, tiles_n, g.group_n, mb, nb);
+            ++tile_iter;
             const int row0 = mb * TILE_M + (int)rank * BM;   // this CTA's rows of the tile
             // J = I0 2^8 + I1: the exact ACC0 and ACC1 sums of this tile's
             // columns in one int64 each; at the end J becomes
@@ -626,16 +711,114 @@ k_split_mma(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
                 }
                 ++chunk_no;
                 if (last) {
-                    // the FP64 results, in place
                     const int nt = nb * BN + colh * CPT;
+                    if constexpr (MODE == EPI_DIRECT) {
+                        // rows adjacent in C: form, record and store each result in one
+                        // pass (the lanes, adjacent rows, write 256 contiguous bytes)
+                        if (row_ok) {
+                            double* cp = g.C + g.c_m[m] + g.c_n[nt];
+                            const int64_t step = g.c_col_stride;
+                            const int64_t cm0 = g.cons_ef ? g.cons_m[m] : 0;
+                            int64_t cur = -1;
+                            int cur_max = 0;
 #pragma unroll
-                    for (int j = 0; j < CPT; ++j) {
-                        const int n = nt + j;
-                        double v = 0.0;
-                        if (row_ok && n < g.N) v = scaled_i64_to_double(J[j], ea + g.eb[n] - 36);
-                        J[j] = __double_as_longlong(v);
+                            for (int j = 0; j < CPT; ++j) {
+                                const int n = nt + j;
+                                if (n < g.N) {
+                                    const double v = scaled_i64_to_double(J[j], ea + g.eb[n] - 36);
+                                    *cp = v;
+                                    if (g.cons_ef) {
+                                        const int64_t crow = cm0 + g.cons_n[n];
+                                        const int ef = (int)(((unsigned long long)__double_as_longlong(v) >> 52) & 0x7FF);
+                                        if (crow != cur) {
+                                            if (cur >= 0 && cur_max) atomicMax(&g.cons_ef[cur], cur_max);
+                                            cur = crow;
+                                            cur_max = ef;
+                                        } else {
+                                            cur_max = max(cur_max, ef);
+                                        }
+                                    }
+                                }
+                                cp += step;
+                            }
+                            if (cur >= 0 && cur_max) atomicMax(&g.cons_ef[cur], cur_max);
+                        }
+                        continue;
                     }
-                    if (g.cons_ef && row_ok) {
+                    if constexpr (MODE == EPI_STAGED) {
+                        // the FP64 results, in place
+#pragma unroll
+                        for (int j = 0; j < CPT; ++j) {
+                            const int n = nt + j;
+                            double v = 0.0;
+                            if (row_ok && n < g.N) v = scaled_i64_to_double(J[j], ea + g.eb[n] - 36);
+                            J[j] = __double_as_longlong(v);
+                        }
+                    }
+                    if constexpr (MODE == EPI_FUSED) {
+                        // fused hand-over: the consumer's rows lie in this tile; a
+                        // warp's lanes and a thread's columns share one of them.  The
+                        // slices follow from V directly, equal to slicing the FP64
+                        // value V 2^(ea + eb - 36) (see fused_fixed_point).
+                        // |V| < 2^53 (K <= 8192) needs no rounding to 53 bits
+                        const bool exact53 = g.v_exact53 != 0;
+                        unsigned tmax = 0;
+#pragma unroll
+                        for (int j = 0; j < CPT; ++j)
+                            if (row_ok && nt + j < g.N)
+                                tmax = max(tmax, (unsigned)(exact53 ? fp64_exponent_field_exact(J[j], ea + g.eb[nt + j] - 36)
+                                                                    : fp64_exponent_field(J[j], ea + g.eb[nt + j] - 36)));
+                        const unsigned wmax = __reduce_max_sync(0xffffffffu, tmax);
+                        // double-buffered by tile parity: a warp may run one tile ahead
+                        const int slot = (int)(tile_iter & 1) * 16 + (row_in_tile / g.rows_per_crow) * (BN / g.cols_per_crow) +
+                                         (colh * CPT) / g.cols_per_crow;
+                        int w_ok = 1;
+                        if (lane == 0) {
+                            atomicMax(&cs_slot[slot], (tile_iter << 11) | wmax);
+                            mbar_arrive(cs_bar);    // release: the maximum above is visible after the wait
+                            w_ok = mbar_wait(cs_bar, (tile_iter - 1) & 1, abort_flag, g.status) ? 1 : 0;
+                        }
+                        ok = __shfl_sync(0xffffffffu, w_ok, 0) != 0;
+                        if (!ok) break;
+                        const unsigned sv = cs_slot[slot];
+                        const int ef = ((sv >> 11) == (tile_iter & 0x1FFFFFu)) ? (int)(sv & 0x7FFu) : 0;
+                        const int e_row = ef ? ef - 1022 : -1022;           // |x| < 2^e_row over the row
+                        if (row_ok && nt < g.N) {
+                            const int64_t crow = g.cons_m[m] + g.cons_n[nt];
+                            if (lane == 0) g.cs_e[crow] = e_row;
+                            // consumer column of this thread's column j: ck_m[m] + ck_n[nt] +
+                            // j ck_stride, with ck_m[m] = the lane's row offset (adjacent
+                            // lanes, adjacent columns): each store writes 64 contiguous bytes
+                            uint16_t* dst = g.cs_out + crow * g.cs_kp + g.ck_m[m] + g.ck_n[nt];
+                            const int64_t step = g.ck_stride, plane = g.cs_plane;
+#pragma unroll
+                            for (int j = 0; j < CPT; ++j) {
+                                const int e2 = ea + g.eb[nt + j] - 36;
+                                long long X = exact53 ? fused_fixed_point_exact<S>(J[j], e2, e_row)
+                                                      : fused_fixed_point<S>(J[j], e2, e_row);
+                                int d[S];
+                                // signed base-256 digits; |X| <= 2^F, so after S - 3 digits
+                                // (S >= 4) the rest fits in 32 bits
+#pragma unroll
+                                for (int p = S - 1; p >= 1; --p) {
+                                    const int lo8 = (int)(((unsigned)X + 128u) & 255u) - 128;   // low bits only
+                                    d[p] = lo8;
+                                    if (p > 2) X = (X - lo8) >> 8;
+                                    else X = ((int)X - lo8) >> 8;
+                                }
+                                d[0] = (int)X;
+#pragma unroll
+                                for (int p = 0; p < S; ++p) {
+                                    // small integer -> FP32 exactly, times 2^-8p; the top half is the BF16
+                                    float f = __int_as_float(0x4B400000 + d[p]) - 12582912.0f;
+                                    if (p > 0) f *= __int_as_float((127 - 8 * p) << 23);
+                                    dst[p * plane] = (uint16_t)(__float_as_uint(f) >> 16);
+                                }
+                                dst += step;
+                            }
+                        }
+                    }
+                    if (MODE == EPI_STAGED && g.cons_ef && row_ok) {
                         // exponent fields of the consumer's rows: run-length maxima
                         // over this thread's columns, one atomic per run
                         const int64_t cm0 = g.cons_m[m];
@@ -658,6 +841,7 @@ k_split_mma(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
                         }
                         if (cur >= 0 && cur_max) atomicMax(&g.cons_ef[cur], cur_max);
                     }
+                    if (MODE == EPI_FUSED) continue;
                     // stores through the warp's 32 x 8 staging tile: lanes of a
                     // quarter-warp then write 8 adjacent columns (64 B) of one row
                     double* stg = staging + ew * (32 * 8);
@@ -840,13 +1024,13 @@ int choose_group_n(int tiles_m, int tiles_n, int grid, int kp, int S) {
     return std::max(1, best);
 }
 
-template <int S, int CG>
-void launch_mma(Ctx& ctx, const CUtensorMap& ta, const CUtensorMap& tb, const MmaArgs& a0) {
+template <int S, int CG, int MODE>
+void launch_mma_k(Ctx& ctx, const CUtensorMap& ta, const CUtensorMap& tb, const MmaArgs& a0) {
     MmaArgs a = a0;
     static std::once_flag once;
     static int max_clusters = 0;
     std::call_once(once, [&ctx] {
-        TRG_CUDA(cudaFuncSetAttribute(k_split_mma<S, CG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        TRG_CUDA(cudaFuncSetAttribute(k_split_mma<S, CG, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       smem_bytes_for(S, CG)));
         if (CG == 2) {
             // pairs that can be resident at once (a persistent grid must not exceed it)
@@ -859,7 +1043,7 @@ void launch_mma(Ctx& ctx, const CUtensorMap& ta, const CUtensorMap& tb, const Mm
             cfg.dynamicSmemBytes = smem_bytes_for(S, CG);
             cfg.attrs = attr;
             cfg.numAttrs = 1;
-            TRG_CUDA(cudaOccupancyMaxActiveClusters(&max_clusters, k_split_mma<S, CG>, &cfg));
+            TRG_CUDA(cudaOccupancyMaxActiveClusters(&max_clusters, k_split_mma<S, CG, MODE>, &cfg));
         }
     });
     const int tiles_m = (a.M + BM * CG - 1) / (BM * CG), tiles_n = (a.N + BN - 1) / BN;
@@ -869,7 +1053,7 @@ void launch_mma(Ctx& ctx, const CUtensorMap& ta, const CUtensorMap& tb, const Mm
     cudaError_t e;
     if (CG == 1) {
         const int grid = ctas;
-        k_split_mma<S, CG><<<grid, THREADS, smem_bytes_for(S, CG), ctx.stream>>>(ta, tb, a);
+        k_split_mma<S, CG, MODE><<<grid, THREADS, smem_bytes_for(S, CG), ctx.stream>>>(ta, tb, a);
         e = cudaGetLastError();
     } else {
         if (max_clusters < 1) fail(TRG_ENOTSUP, "split MMA: no CTA pair fits on this device");
@@ -884,19 +1068,26 @@ void launch_mma(Ctx& ctx, const CUtensorMap& ta, const CUtensorMap& tb, const Mm
         cfg.stream = ctx.stream;
         cfg.attrs = attr;
         cfg.numAttrs = 1;
-        e = cudaLaunchKernelEx(&cfg, k_split_mma<S, CG>, ta, tb, a);
+        e = cudaLaunchKernelEx(&cfg, k_split_mma<S, CG, MODE>, ta, tb, a);
         if (e == cudaSuccess) e = cudaGetLastError();
     }
     ctx.launches++;
     if (e != cudaSuccess) {
         cudaFuncAttributes fa;
-        cudaFuncGetAttributes(&fa, k_split_mma<S, CG>);
+        cudaFuncGetAttributes(&fa, k_split_mma<S, CG, MODE>);
         fail(TRG_ECUDA, std::string("split MMA launch: ") + cudaGetErrorString(e) + " (regs " +
                             std::to_string(fa.numRegs) + ", max threads " + std::to_string(fa.maxThreadsPerBlock) +
                             ", dyn smem " + std::to_string(smem_bytes_for(S, CG)) + " / " +
                             std::to_string(fa.maxDynamicSharedSizeBytes) + ", local " +
                             std::to_string(fa.localSizeBytes) + ")");
     }
+}
+
+template <int S, int CG>
+void launch_mma(Ctx& ctx, const CUtensorMap& ta, const CUtensorMap& tb, const MmaArgs& a) {
+    if (a.cs_out) launch_mma_k<S, CG, EPI_FUSED>(ctx, ta, tb, a);
+    else if (a.c_rows_fast) launch_mma_k<S, CG, EPI_DIRECT>(ctx, ta, tb, a);
+    else launch_mma_k<S, CG, EPI_STAGED>(ctx, ta, tb, a);
 }
 
 template <int S>
@@ -926,6 +1117,12 @@ static Gather transpose_gather(const Gather& b, const int64_t* off_k, const int6
     return t;
 }
 
+int64_t split_rows_padded(const Ctx& ctx, int64_t M) {
+    const int64_t tile = (ctx.cfg.mma_pairs && M > BM) ? 2 * BM : BM;
+    return (M + tile - 1) / tile * tile;
+}
+int64_t split_k_padded(int64_t K) { return (std::max<int64_t>(K, 1) + BK - 1) / BK * BK; }
+
 void gemm_split(Ctx& ctx, const GemmDesc& d) {
     if (d.M <= 0 || d.N <= 0) return;
     if (d.beta != 0.0) fail(TRG_EINVAL, "split GEMM overwrites its output (beta must be 0)");
@@ -934,25 +1131,27 @@ void gemm_split(Ctx& ctx, const GemmDesc& d) {
     const int M = (int)d.M, N = (int)d.N, K = (int)std::max<int64_t>(d.K, 1);
     // CTA pairs (256-row tiles) once A has more than one 128-row block
     const int CG = (ctx.cfg.mma_pairs && M > BM) ? 2 : 1;
-    const int Mp = (M + BM * CG - 1) / (BM * CG) * (BM * CG), Np = (N + BN - 1) / BN * BN,
-              Kp = (K + BK - 1) / BK * BK;
+    const int Mp = (int)split_rows_padded(ctx, M), Np = (N + BN - 1) / BN * BN, Kp = (int)split_k_padded(K);
+    const bool pre_a = d.a_slices != nullptr;    // A arrives sliced from its producer
 
-    // scratch: exponents + slices of A and B
+    // scratch: exponents + slices of A (unless given) and B
     const size_t bytes_e = (size_t)(Mp + Np) * sizeof(int);
-    const size_t bytes_a = (size_t)S * Mp * Kp * 2, bytes_b = (size_t)S * Np * Kp * 2;
+    const size_t bytes_a = pre_a ? 0 : (size_t)S * Mp * Kp * 2, bytes_b = (size_t)S * Np * Kp * 2;
     ctx.ensure(ctx.split_ws, bytes_e + bytes_a + bytes_b + 1024);
     uint8_t* base = ctx.split_ws.as<uint8_t>();
-    int* ea = (int*)base;
-    int* eb = ea + Mp;
-    uint16_t* sa = (uint16_t*)(base + ((bytes_e + 255) & ~(size_t)255));
-    uint16_t* sb = sa + (size_t)S * Mp * Kp;
+    int* ea = pre_a ? const_cast<int*>(d.a_e) : (int*)base;
+    int* eb = (int*)base + Mp;
+    uint16_t* sa = pre_a ? const_cast<uint16_t*>(d.a_slices) : (uint16_t*)(base + ((bytes_e + 255) & ~(size_t)255));
+    uint16_t* sb = (uint16_t*)(base + ((bytes_e + 255) & ~(size_t)255)) + (pre_a ? 0 : (size_t)S * Mp * Kp);
 
     // B as rows n, columns k: element (n, k) at B[b_k[k] + b_n[n]]
     const Gather bt = transpose_gather(d.B, d.B.off_r, d.B.off_c);
     Gather bt2 = bt;
     bt2.c_fast = false;
     // contiguous along k in memory?  (the k-table of B is B.off_r)
-    if (d.a_ef) {
+    if (pre_a) {
+        // slices and exponents of A were written by the producing product
+    } else if (d.a_ef) {
         // the producing product already recorded A's exponent fields
         TRG_CUDA(cudaMemcpyAsync(ea, d.a_ef, (size_t)M * sizeof(int), cudaMemcpyDeviceToDevice, ctx.stream));
         k_exponent_finish<<<(unsigned)((M + 255) / 256), 256, 0, ctx.stream>>>(ea, M);
@@ -962,10 +1161,14 @@ void gemm_split(Ctx& ctx, const GemmDesc& d) {
     }
     row_exponents(ctx, bt2, N, K, eb);
     switch (S) {
-        case 2: launch_slice<2>(ctx, d.A, M, K, Mp, Kp, ea, sa); launch_slice<2>(ctx, bt2, N, K, Np, Kp, eb, sb); break;
-        case 3: launch_slice<3>(ctx, d.A, M, K, Mp, Kp, ea, sa); launch_slice<3>(ctx, bt2, N, K, Np, Kp, eb, sb); break;
-        case 4: launch_slice<4>(ctx, d.A, M, K, Mp, Kp, ea, sa); launch_slice<4>(ctx, bt2, N, K, Np, Kp, eb, sb); break;
-        case 5: launch_slice<5>(ctx, d.A, M, K, Mp, Kp, ea, sa); launch_slice<5>(ctx, bt2, N, K, Np, Kp, eb, sb); break;
+        case 2: if (!pre_a) launch_slice<2>(ctx, d.A, M, K, Mp, Kp, ea, sa);
+                launch_slice<2>(ctx, bt2, N, K, Np, Kp, eb, sb); break;
+        case 3: if (!pre_a) launch_slice<3>(ctx, d.A, M, K, Mp, Kp, ea, sa);
+                launch_slice<3>(ctx, bt2, N, K, Np, Kp, eb, sb); break;
+        case 4: if (!pre_a) launch_slice<4>(ctx, d.A, M, K, Mp, Kp, ea, sa);
+                launch_slice<4>(ctx, bt2, N, K, Np, Kp, eb, sb); break;
+        case 5: if (!pre_a) launch_slice<5>(ctx, d.A, M, K, Mp, Kp, ea, sa);
+                launch_slice<5>(ctx, bt2, N, K, Np, Kp, eb, sb); break;
         default: fail(TRG_EINVAL, "split_slices must be 2..5");
     }
     const CUtensorMap ta = make_map(sa, S * Mp, Kp);
@@ -975,6 +1178,21 @@ void gemm_split(Ctx& ctx, const GemmDesc& d) {
     a.ea = ea; a.eb = eb; a.C = d.C; a.c_m = d.c_m; a.c_n = d.c_n;
     a.status = ctx.status.as<int>();
     a.cons_ef = d.cons_ef; a.cons_m = d.cons_m; a.cons_n = d.cons_n;
+    a.cs_out = d.cs_out; a.cs_plane = d.cs_mp * d.cs_kp; a.cs_kp = d.cs_kp; a.cs_e = d.cs_e;
+    a.ck_m = d.ck_m; a.ck_n = d.ck_n; a.rows_per_crow = d.rows_per_crow; a.cols_per_crow = d.cols_per_crow;
+    a.ck_stride = d.ck_stride; a.c_rows_fast = d.c_rows_fast ? 1 : 0; a.c_col_stride = d.c_col_stride;
+    // |V| <= (K / 512) (2^32 + 2^24) 2^14 + 2 K 2^20 < 2^53 for K <= 8192
+    a.v_exact53 = Kp <= 8192 ? 1 : 0;
+    if (d.cs_out) {
+        // a consumer row = rows_per_crow consecutive rows (32, 64 or 128, so a
+        // warp's lanes and the CTA's 128-row tile hold whole groups) times
+        // cols_per_crow consecutive columns (so a thread's 32 hold one group)
+        auto pow2_32_128 = [](int v) { return v == 32 || v == 64 || v == 128; };
+        const bool shape_ok = pow2_32_128(d.rows_per_crow) && pow2_32_128(d.cols_per_crow) &&
+                              M % d.rows_per_crow == 0 && N % d.cols_per_crow == 0 && d.cs_kp % 8 == 0 &&
+                              d.cons_m && d.cons_n && d.ck_m && d.ck_n && d.cs_e;
+        if (!shape_ok) fail(TRG_EINVAL, "fused slice hand-over: consumer rows do not tile");
+    }
     const int tok = ctx.region_begin(TRG_PHASE_MMA);
     switch (S * 2 + CG - 1) {
         case 4: launch_mma<2, 1>(ctx, ta, tb, a); break;
@@ -1121,14 +1339,17 @@ extern "C" int trg_gemm_noalloc(int M, int N, int K, const double* A, int lda, c
         a.M = M; a.N = N; a.Kp = Kp; a.Mp = Mp; a.Np = Np; a.S = S;
         a.ea = ea; a.eb = eb; a.C = C; a.c_m = cm; a.c_n = cn; a.status = status;
         a.cons_ef = nullptr; a.cons_m = nullptr; a.cons_n = nullptr;
+        a.cs_out = nullptr; a.cs_plane = 0; a.cs_kp = 0; a.cs_e = nullptr; a.ck_m = nullptr; a.ck_n = nullptr;
+        a.rows_per_crow = a.cols_per_crow = 0;
+        a.ck_stride = 0; a.c_rows_fast = 0; a.c_col_stride = 0; a.v_exact53 = 0;
         const int tiles = ((M + BM - 1) / BM) * ((N + BN - 1) / BN);
         const int grid = std::max(1, std::min(tiles, sms));
         a.group_n = choose_group_n((M + BM - 1) / BM, (N + BN - 1) / BN, grid, Kp, S);
         switch (S) {
 #define TRG_NOALLOC_MMA(SS)                                                                                  \
-    TRG_CUDA(cudaFuncSetAttribute(k_split_mma<SS, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,           \
+    TRG_CUDA(cudaFuncSetAttribute(k_split_mma<SS, 1, EPI_STAGED>, cudaFuncAttributeMaxDynamicSharedMemorySize,           \
                                   smem_bytes_for(SS, 1)));                                                   \
-    k_split_mma<SS, 1><<<grid, THREADS, smem_bytes_for(SS, 1), stream>>>(ta, tbm, a);                        \
+    k_split_mma<SS, 1, EPI_STAGED><<<grid, THREADS, smem_bytes_for(SS, 1), stream>>>(ta, tbm, a);                        \
     break;
             case 2: TRG_NOALLOC_MMA(2)
             case 3: TRG_NOALLOC_MMA(3)

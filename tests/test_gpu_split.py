@@ -126,3 +126,32 @@ def test_split_solve_matches_oracle(torch, name, s):
         sv.coarse_grain(g["dcut"], g["nsteps"])
         f, _ = sv.free_energy()
     assert abs(f - g["f"]) <= F_TOL_SPLIT, (f, g["f"], abs(f - g["f"]))
+
+
+@pytest.mark.parametrize("dx,dy,dn,ws", [(32, 32, 40, 0), (64, 32, 48, 0), (32, 64, 24, 0),
+                                         (64, 64, 20, 200_000_000)])
+def test_fused_handover_is_bit_identical(torch, dx, dy, dn, ws):
+    # the producer writing the next product's slices must give exactly what
+    # slicing its FP64 output gives (several j-blocks, a ragged last one)
+    t = workloads.random_tensor((dx, dy, dx, dy), seed=800 + dx + dy)
+    u = workloads.random_isometry(dx, dn, seed=900 + dn)
+    tt, uu = torch.from_numpy(t).cuda(), torch.from_numpy(u).cuda()
+    outs = []
+    for fused in (0, 1, 2):
+        with Solver(0, precision="split", fused_slices=fused, workspace_bytes=ws) as sv:
+            outs.append(sv.contract(tt, uu))
+    assert torch.equal(outs[0], outs[1])
+    assert torch.equal(outs[0], outs[2])
+    ref = hotrg.contract_x(t, u)
+    assert np.abs(outs[1].cpu().numpy() - ref).max() <= 1e-7 * np.abs(ref).max()
+
+
+def test_fused_handover_solve_is_bit_identical(torch):
+    # a solve whose bond dimension reaches 32 (x and rotated y half-steps)
+    res = []
+    for fused in (0, 1, 2):
+        with Solver(0, precision="split", fused_slices=fused) as sv:
+            sv.init_tensor("ising", 0.44, 0.0)
+            sv.coarse_grain(32, 12)
+            res.append(sv.free_energy())
+    assert res[0] == res[1] == res[2]
