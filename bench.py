@@ -176,6 +176,25 @@ def load_peaks():
         return {}
 
 
+# DRAM bytes (read + write) per k_split_mma launch, averaged over the launches
+# of two timed half-steps of this workload, from the ncu capture summarised in
+# profiles/split_mma_dram_hotrg_ising_dcut64_s4.md.  The figure describes the
+# kernel source it was taken on: reported only while that file is unchanged.
+SPLIT_MMA_TRAFFIC = {"sha256": "03dda785d64ee1102701a9c38b21d1a62520b57ca25d33e2fbba0e03910c01b7",
+                     "bytes_per_launch": 5.148e9}
+
+
+def split_mma_traffic():
+    import hashlib
+    src = os.path.join(os.path.dirname(os.path.abspath(__file__)), "paper_2306_00358_gb300", "csrc", "split_gemm.cu")
+    try:
+        with open(src, "rb") as f:
+            digest = hashlib.sha256(f.read()).hexdigest()
+    except OSError:
+        return None
+    return SPLIT_MMA_TRAFFIC["bytes_per_launch"] if digest == SPLIT_MMA_TRAFFIC["sha256"] else None
+
+
 def run_native(args):
     import numpy as np
     import torch
@@ -253,7 +272,7 @@ def run_native(args):
         achieved = per_launch / t_launch / 1e12 if t_launch > 0 else 0.0
         peak = peaks.get("bf16_tflops_sustained", 1722.5)
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": None, "kernel": "k_split_mma (BF16 slice products)",
+                "frac": achieved / peak, "traffic": split_mma_traffic(), "kernel": "k_split_mma (BF16 slice products)",
                 "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained (of measured)"}
 
     # end to end through the C ABI with host buffers
