@@ -195,6 +195,27 @@ def split_mma_traffic():
     return SPLIT_MMA_TRAFFIC["bytes_per_launch"] if digest == SPLIT_MMA_TRAFFIC["sha256"] else None
 
 
+def replica_beta(rank: int) -> float:
+    """Each rank solves its own coupling (replicas; the path has no exchange)."""
+    return BETA_C * (1.0 + 1e-4 * rank)
+
+
+def max_over_ranks(ms: float, world: int, device: str = "cuda") -> float:
+    """The slowest rank's time of the timed region (all ranks take part)."""
+    if world <= 1:
+        return float(ms)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def seconds_per_half_step(ms_max: float, steps: int, world: int) -> float:
+    """Whole-job throughput: all ranks' half-steps over the slowest rank's time."""
+    return ms_max / 1e3 / (steps * world)
+
+
 def run_native(args):
     import numpy as np
     import torch
@@ -220,8 +241,7 @@ def run_native(args):
     stream = torch.cuda.current_stream()
     s = Solver(local, stream=stream, precision=precision, split_slices=args.slices, mma_pairs=args.mma_pairs,
                fused_slices=args.fused_slices)
-    # replicas: every rank solves its own coupling (beta_c shifted per rank)
-    beta = BETA_C * (1.0 + 1e-4 * rank)
+    beta = replica_beta(rank)
     s.init_tensor("ising", beta, 0.0)
     s.coarse_grain(DCUT, STEADY_AT)
     s.coarse_grain(DCUT, warmup)
@@ -246,11 +266,8 @@ def run_native(args):
     counters = {k: v - counters0[k] for k, v in s.counters().items()}
     ph = s.phase_stats()
     s.profile(False)
-    t_max = torch.tensor([ms], dtype=torch.float64, device="cuda")
-    if world > 1:
-        dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
-    ms_max = float(t_max.item())
-    sec_per_step = ms_max / 1e3 / (steps * world)
+    ms_max = max_over_ranks(ms, world)
+    sec_per_step = seconds_per_half_step(ms_max, steps, world)
 
     # roofline of the dominant kernel: the D^7 product
     peaks = load_peaks()
