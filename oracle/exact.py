@@ -141,6 +141,42 @@ def ising_lnz_exact(width: int, height: int, beta: float, h: float = 0.0) -> flo
     return emax + math.log(float(np.sum(np.exp(e - emax))))
 
 
+def ising_magnetization_exact(width: int, height: int, beta: float, h: float = 0.0) -> float:
+    """<(1/V) sum_i s_i> on a width x height torus by enumeration."""
+    nsite = width * height
+    if nsite > 24:
+        raise ValueError("lattice too large to enumerate")
+    states = np.arange(2 ** nsite, dtype=np.int64)
+    s = (1 - 2 * ((states[:, None] >> np.arange(nsite)) & 1)).reshape(-1, height, width)
+    bond = np.sum(s * np.roll(s, -1, axis=2), axis=(1, 2)) + np.sum(s * np.roll(s, -1, axis=1), axis=(1, 2))
+    mag = np.sum(s, axis=(1, 2))
+    e = beta * bond + beta * h * mag
+    w = np.exp(e - np.max(e))
+    return float(np.sum(w * mag) / np.sum(w)) / nsite
+
+
+def potts_fraction0_exact(width: int, height: int, beta: float, h: float = 0.0, q: int = 3) -> float:
+    """<(1/V) sum_i [s_i = 0]> on a torus by enumeration."""
+    nsite = width * height
+    if q ** nsite > 5e7:
+        raise ValueError("lattice too large to enumerate")
+    states = np.arange(q ** nsite, dtype=np.int64)
+    s = ((states[:, None] // (q ** np.arange(nsite))) % q).reshape(-1, height, width)
+    same = np.sum(s == np.roll(s, -1, axis=2), axis=(1, 2)) + np.sum(s == np.roll(s, -1, axis=1), axis=(1, 2))
+    zeros = np.sum(s == 0, axis=(1, 2))
+    e = beta * same + beta * h * zeros
+    w = np.exp(e - np.max(e))
+    return float(np.sum(w * zeros) / np.sum(w)) / nsite
+
+
+def onsager_yang_magnetization(beta: float) -> float:
+    """Spontaneous magnetization of the square-lattice Ising model (Yang 1952):
+    M = (1 - sinh(2 beta)^-4)^(1/8) for beta > beta_c, else 0."""
+    if beta <= BETA_C:
+        return 0.0
+    return (1.0 - math.sinh(2.0 * beta) ** -4) ** 0.125
+
+
 def potts_lnz_exact(width: int, height: int, beta: float, h: float = 0.0, q: int = 3) -> float:
     """ln Z of the q-state Potts model on a torus by enumeration:
     Z = sum_s exp(beta * #(equal neighbour pairs) + beta h * #(sites in state 0))."""
@@ -157,17 +193,33 @@ def potts_lnz_exact(width: int, height: int, beta: float, h: float = 0.0, q: int
     return emax + math.log(float(np.sum(np.exp(e - emax))))
 
 
+def xy_cos_exact(width: int, height: int, beta: float, h: float = 0.0, d0: int = 9) -> float:
+    """<cos theta> of the charge-truncated XY model on a torus: the charge
+    sum with the site factor of site (0, 0) replaced by
+    (I_{div-1}(beta h) + I_{div+1}(beta h)) / 2, divided by Z (all sites
+    are equivalent on the torus)."""
+    return math.exp(_xy_log_charge_sum(width, height, beta, h, d0, impure_site=True) -
+                    _xy_log_charge_sum(width, height, beta, h, d0, impure_site=False))
+
+
 def xy_lnz_exact(width: int, height: int, beta: float, h: float = 0.0, d0: int = 9) -> float:
     """ln Z of the charge-truncated XY model (|n| <= (d0-1)/2) on a torus, by
     summing over all bond charges of the character expansion:
     Z = sum_n prod_bonds I_n(beta) prod_sites I_div(beta h),
     div = n_left + n_up - n_right - n_down at each site."""
+    return _xy_log_charge_sum(width, height, beta, h, d0, impure_site=False)
+
+
+def _xy_log_charge_sum(width: int, height: int, beta: float, h: float, d0: int, impure_site: bool) -> float:
     nmax = d0 // 2
     charges = np.arange(-nmax, nmax + 1)
     ib = np.array([bessel_i(int(n), beta) for n in charges])
     ndiv = 4 * nmax
     isite = {int(m): bessel_i(int(m), beta * h) for m in range(-ndiv, ndiv + 1)}
     site_tab = np.array([isite[m] for m in range(-ndiv, ndiv + 1)])
+    # site (0, 0) with cos(theta) inserted (the charge sum may be negative then)
+    imp_tab = np.array([0.5 * (bessel_i(m - 1, beta * h) + bessel_i(m + 1, beta * h))
+                        for m in range(-ndiv, ndiv + 1)])
     nsite = width * height
     nbond = 2 * nsite
     if d0 ** nbond > 2e8:
@@ -191,6 +243,7 @@ def xy_lnz_exact(width: int, height: int, beta: float, h: float = 0.0, d0: int =
                 n_u = n[nsite + y * width + x]
                 n_d = n[nsite + ((y - 1) % height) * width + x]
                 div = n_l + n_u - n_r - n_d
-                w = w * site_tab[np.asarray(div) + ndiv]
+                tab = imp_tab if (impure_site and x == 0 and y == 0) else site_tab
+                w = w * tab[np.asarray(div) + ndiv]
         total += float(np.sum(w))
     return math.log(total)

@@ -111,13 +111,29 @@ def contract_x(t: np.ndarray, u: np.ndarray, j_chunk: int | None = None) -> np.n
     return out
 
 
-def contract_x_slice(t: np.ndarray, u: np.ndarray, j0: int, j1: int) -> np.ndarray:
-    """Tx[:, j0:j1, :, :] of contract_x."""
+def contract_x_slice(t: np.ndarray, u: np.ndarray, j0: int, j1: int,
+                     bottom: np.ndarray | None = None) -> np.ndarray:
+    """Tx[:, j0:j1, :, :] of contract_x; `bottom` (default t) is the lower
+    tensor t[a,c,e,l] of the pair, t the upper one t[b,j,d,c]."""
+    if bottom is None:
+        bottom = t
     tj = t[:, j0:j1]                                   # (b, j, d, c)
     x1 = np.tensordot(u, tj, axes=([1], [0]))          # (a, i, j, d, c)
-    x2 = np.tensordot(x1, t, axes=([0, 4], [0, 1]))    # (i, j, d, e, l)
+    x2 = np.tensordot(x1, bottom, axes=([0, 4], [0, 1]))   # (i, j, d, e, l)
     x3 = np.tensordot(x2, u, axes=([2, 3], [1, 0]))    # (i, j, l, k)
     return x3.transpose(0, 1, 3, 2)
+
+
+def contract_pair_x(top: np.ndarray, bottom: np.ndarray, u: np.ndarray) -> np.ndarray:
+    """Tx[i,j,k,l] = sum U[a,b,i] top[b,j,d,c] bottom[a,c,e,l] U[e,d,k]: the
+    x blocking of two different tensors (an impure one with a pure one)."""
+    dn, dy = u.shape[2], top.shape[1]
+    out = np.empty((dn, dy, dn, dy))
+    j_chunk = max(1, min(dy, int(2 ** 27 // max(1, top.shape[0] ** 2 * dn * dy))))
+    for j0 in range(0, dy, j_chunk):
+        j1 = min(dy, j0 + j_chunk)
+        out[:, j0:j1] = contract_x_slice(top, u, j0, j1, bottom=bottom)
+    return out
 
 
 def rotate_in(t: np.ndarray) -> np.ndarray:
@@ -153,6 +169,31 @@ def half_step(t: np.ndarray, dcut: int, direction: str, trunc: str = "paper",
     raise ValueError("direction must be 'x' or 'y'")
 
 
+def half_step_impure(t: np.ndarray, t_imp: np.ndarray, dcut: int, direction: str, trunc: str = "paper",
+                     gap_tol: float = 1e-6):
+    """One half-step of the pure tensor and of an impure one blocked with it.
+
+    The isometry comes from the pure tensor's environment (the impure tensor
+    is one site in the whole lattice and leaves it unchanged); the impure
+    block is the mean of the two placements of the impurity in the pair,
+    (C(imp, pure) + C(pure, imp)) / 2, so after N half-steps it is the mean
+    of the insertion over all 2^N sites of the block."""
+    if direction == "x":
+        m = environment_x(t)
+        u, lam = isometry(m, dcut, trunc, gap_tol)
+        pure = contract_x(t, u)
+        imp = 0.5 * (contract_pair_x(t_imp, t, u) + contract_pair_x(t, t_imp, u))
+        return HalfStep(pure, lam, u.shape[2], u), imp
+    if direction == "y":
+        r, ri = rotate_in(t), rotate_in(t_imp)
+        m = environment_x(r)
+        u, lam = isometry(m, dcut, trunc, gap_tol)
+        pure = rotate_out(contract_x(r, u))
+        imp = rotate_out(0.5 * (contract_pair_x(ri, r, u) + contract_pair_x(r, ri, u)))
+        return HalfStep(pure, lam, u.shape[2], u), imp
+    raise ValueError("direction must be 'x' or 'y'")
+
+
 def trace_pbc(t: np.ndarray) -> float:
     """Tr T = sum_{i,j} T[i, j, i, j]: one tensor closed on itself."""
     return float(np.einsum("ijij->", t))
@@ -171,26 +212,33 @@ class Solve:
     f: float = float("nan")
     trace: float = float("nan")
     tensor: np.ndarray | None = None
+    expectation: float = float("nan")              # Tr T_imp / Tr T when an impure tensor ran along
 
 
 def solve(t0: np.ndarray, beta: float, dcut: int, nsteps: int, trunc: str = "paper",
           gap_tol: float = 1e-6, norm: str = "halfstep", keep_full_spectra: bool = False,
-          first_direction: str = "x") -> Solve:
+          first_direction: str = "x", impure: np.ndarray | None = None) -> Solve:
     """Run nsteps alternating half-steps (x first) from the raw tensor t0 and
     return ln Z / V and f = -(ln Z / V) / beta for the periodic lattice of
-    2^nsteps sites that the final trace closes."""
+    2^nsteps sites that the final trace closes.  With an impure tensor (t0
+    with an observable inserted) it is blocked alongside, divided by the same
+    norms, and expectation = Tr T_imp / Tr T is the site mean of <O>."""
     t = np.array(t0, dtype=np.float64)
     n0 = float(np.max(np.abs(t)))
     if not n0 > 0:
         raise ValueError("initial tensor is zero")
     t = t / n0
+    t_imp = None if impure is None else np.array(impure, dtype=np.float64) / n0
     res = Solve(beta=beta, ln_n0=math.log(n0))
     lnz = math.log(n0)
     # a tensor after half-step k stands for 2^k sites, so its norm enters
     # ln Z / V with weight 2^-k whichever schedule divides it out
     directions = ("x", "y") if first_direction == "x" else ("y", "x")
     for k in range(1, nsteps + 1):
-        hs = half_step(t, dcut, directions[(k - 1) % 2], trunc, gap_tol)
+        if t_imp is None:
+            hs = half_step(t, dcut, directions[(k - 1) % 2], trunc, gap_tol)
+        else:
+            hs, t_imp = half_step_impure(t, t_imp, dcut, directions[(k - 1) % 2], trunc, gap_tol)
         t = hs.tensor
         res.spectra.append(hs.lam[:hs.dn].copy())
         if keep_full_spectra:
@@ -201,6 +249,8 @@ def solve(t0: np.ndarray, beta: float, dcut: int, nsteps: int, trunc: str = "pap
             if not (nk > 0 and math.isfinite(nk)):
                 raise FloatingPointError(f"non-positive norm at half-step {k}")
             t = t / nk
+            if t_imp is not None:
+                t_imp = t_imp / nk
             res.ln_norms.append(math.log(nk))
             lnz += math.ldexp(math.log(nk), -k)
         elif norm == "paper":
@@ -210,6 +260,8 @@ def solve(t0: np.ndarray, beta: float, dcut: int, nsteps: int, trunc: str = "pap
                 if not (nk > 0 and math.isfinite(nk)):
                     raise FloatingPointError(f"non-positive norm at half-step {k}")
                 t = t / nk
+                if t_imp is not None:
+                    t_imp = t_imp / nk
                 res.ln_norms.append(math.log(nk))
                 lnz += math.ldexp(math.log(nk), -k)
             else:
@@ -224,4 +276,6 @@ def solve(t0: np.ndarray, beta: float, dcut: int, nsteps: int, trunc: str = "pap
     res.lnz_per_site = lnz
     res.f = -lnz / beta if beta > 0 else float("nan")
     res.tensor = t
+    if t_imp is not None:
+        res.expectation = trace_pbc(t_imp) / tr
     return res

@@ -114,6 +114,57 @@ def potts_tensor(beta: float, h: float = 0.0, q: int = 3) -> np.ndarray:
     return t
 
 
+# ------------------------------------------------------- impure tensors ---
+# The site tensor with an observable O(s) inserted at its site: the same sum
+# over the site's spin with O as an extra factor.  Ising: O = s; XY: O =
+# cos(theta), which in the character expansion turns the site factor
+# I_div(beta h) into (I_{div-1}(beta h) + I_{div+1}(beta h)) / 2 (from
+# cos(theta) = (e^{i theta} + e^{-i theta}) / 2); Potts: O = [s = 0].
+
+def ising_impure_tensor(beta: float, h: float = 0.0) -> np.ndarray:
+    """Ising site tensor with the spin s inserted, shape (2, 2, 2, 2)."""
+    w = ising_weight_sqrt(beta)
+    t = np.zeros((2, 2, 2, 2))
+    for s_idx, s in enumerate((1.0, -1.0)):
+        ws = w[s_idx]
+        t += s * math.exp(beta * h * s) * np.einsum("i,j,k,l->ijkl", ws, ws, ws, ws)
+    return t
+
+
+def xy_impure_tensor(beta: float, h: float = 0.0, d0: int = 9) -> np.ndarray:
+    """XY site tensor with cos(theta) inserted, shape (d0,)*4."""
+    nmax = d0 // 2
+    charges = np.arange(-nmax, nmax + 1)
+    leg = np.array([math.sqrt(bessel_i(n, beta)) for n in charges])
+    t = np.zeros((d0, d0, d0, d0))
+    for a, nl in enumerate(charges):
+        for b, nu in enumerate(charges):
+            for c, nr in enumerate(charges):
+                for d, nd in enumerate(charges):
+                    div = nl + nu - nr - nd
+                    site = 0.5 * (bessel_i(div - 1, beta * h) + bessel_i(div + 1, beta * h))
+                    t[a, b, c, d] = leg[a] * leg[b] * leg[c] * leg[d] * site
+    return t
+
+
+def potts_impure_tensor(beta: float, h: float = 0.0, q: int = 3) -> np.ndarray:
+    """q-state Potts site tensor with [s = 0] inserted: only the s = 0 term."""
+    L = potts_weight_factor(beta, q)
+    l0 = L[0]
+    return math.exp(beta * h) * np.einsum("i,j,k,l->ijkl", l0, l0, l0, l0)
+
+
+def impure_tensor(model: str, beta: float, h: float = 0.0, d0: int | None = None) -> np.ndarray:
+    model = model.lower()
+    if model == "ising":
+        return ising_impure_tensor(beta, h)
+    if model == "xy":
+        return xy_impure_tensor(beta, h, 9 if d0 is None else d0)
+    if model == "potts":
+        return potts_impure_tensor(beta, h, 3 if d0 is None else d0)
+    raise ValueError(f"unknown model {model!r}")
+
+
 def initial_tensor(model: str, beta: float, h: float = 0.0, d0: int | None = None) -> np.ndarray:
     model = model.lower()
     if model == "ising":

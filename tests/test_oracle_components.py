@@ -184,3 +184,23 @@ def test_potts_enumeration_known_cases():
     beta = 0.9
     ref = exact.ising_lnz_exact(2, 2, beta / 2) + 8 * beta / 2
     assert exact.potts_lnz_exact(2, 2, beta, q=2) == pytest.approx(ref, abs=1e-12)
+
+
+def test_impure_tensors_reduce_to_pure_ones():
+    # inserting O = 1 gives the pure tensor: Ising s = +-1 splits it in two
+    # signed halves, Potts [s = 0] is one of the q terms, and the XY site
+    # factor (I_{n-1} + I_{n+1}) / 2 equals I_n'(x) (the recurrence of I_n)
+    from oracle import models
+    beta, h = 0.7, 0.3
+    t = models.ising_tensor(beta, h)
+    ti = models.ising_impure_tensor(beta, h)
+    w = models.ising_weight_sqrt(beta)
+    plus = math.exp(beta * h) * np.einsum("i,j,k,l->ijkl", w[0], w[0], w[0], w[0])
+    assert np.abs(t + ti - 2 * plus).max() <= 1e-14 * np.abs(t).max()
+    tp = models.potts_tensor(beta, 0.0, 3)
+    total = sum(np.einsum("i,j,k,l->ijkl", *(models.potts_weight_factor(beta, 3)[s],) * 4) for s in range(3))
+    assert np.allclose(tp, total, rtol=1e-14)
+    x = beta * h
+    for n in range(-3, 4):
+        deriv = (models.bessel_i(n, x + 1e-6) - models.bessel_i(n, x - 1e-6)) / 2e-6
+        assert abs(0.5 * (models.bessel_i(n - 1, x) + models.bessel_i(n + 1, x)) - deriv) <= 1e-8

@@ -176,3 +176,52 @@ def test_potts_q2_is_ising_onsager():
     sol = hotrg.solve(models.potts_tensor(beta, 0.0, 2), beta, 16, 40)
     ref = exact.onsager_integral(beta / 2) + beta
     assert abs(sol.lnz_per_site - ref) <= 1e-9
+
+
+# ------------------------------------------------ impure tensors (observables) ---
+@pytest.mark.parametrize("nsteps", [2, 3, 4])
+@pytest.mark.parametrize("beta,h", [(0.44, 0.01), (0.3, -0.25), (0.6, 0.0)])
+def test_ising_magnetization_matches_enumeration(nsteps, beta, h):
+    width, height = exact.hotrg_block(nsteps)
+    sol = hotrg.solve(models.ising_tensor(beta, h), beta, NO_TRUNC, nsteps,
+                      impure=models.ising_impure_tensor(beta, h))
+    ref = exact.ising_magnetization_exact(width, height, beta, h)
+    assert abs(sol.expectation - ref) <= 1e-12
+
+
+@pytest.mark.parametrize("nsteps", [1, 2])
+def test_xy_cos_matches_enumeration(nsteps):
+    width, height = exact.hotrg_block(nsteps)
+    beta, h = 0.9, 0.1
+    sol = hotrg.solve(models.xy_tensor(beta, h, 5), beta, NO_TRUNC, nsteps,
+                      impure=models.xy_impure_tensor(beta, h, 5))
+    assert abs(sol.expectation - exact.xy_cos_exact(width, height, beta, h, 5)) <= 1e-12
+
+
+@pytest.mark.parametrize("nsteps", [2, 3])
+def test_potts_fraction_matches_enumeration(nsteps):
+    width, height = exact.hotrg_block(nsteps)
+    beta, h = 0.8, 0.05
+    sol = hotrg.solve(models.potts_tensor(beta, h, 3), beta, NO_TRUNC, nsteps,
+                      impure=models.potts_impure_tensor(beta, h, 3))
+    assert abs(sol.expectation - exact.potts_fraction0_exact(width, height, beta, h, 3)) <= 1e-12
+
+
+def test_magnetization_vanishes_in_the_symmetric_phase():
+    # h = 0: the impure tensor is odd under the global spin flip, the
+    # isometries keep the two sectors apart, so the trace is zero
+    sol = hotrg.solve(models.ising_tensor(0.3), 0.3, 8, 20, impure=models.ising_impure_tensor(0.3))
+    assert abs(sol.expectation) <= 1e-14
+
+
+def test_spontaneous_magnetization_approaches_yang():
+    # beta > beta_c with a field that only picks the + state on 2^20 x 2^20
+    # sites: M -> (1 - sinh(2 beta)^-4)^(1/8), the error shrinking with Dcut
+    beta, h = 0.6, 1e-10
+    ref = exact.onsager_yang_magnetization(beta)
+    err = {}
+    for dcut in (8, 16):
+        sol = hotrg.solve(models.ising_tensor(beta, h), beta, dcut, 40, impure=models.ising_impure_tensor(beta, h))
+        err[dcut] = abs(sol.expectation - ref)
+    assert err[16] <= 5e-6
+    assert err[16] < err[8] / 4
