@@ -135,6 +135,31 @@ int trg_init_tensor(trg_ctx* ctx, int model, double beta, double h, int D0);
 int trg_init_tensor_raw(trg_ctx* ctx, const double* T_host, int Dx, int Dy, double beta);
 
 /*
+ * Impure tensor: the initial tensor with an observable O inserted at its
+ * site, coarse-grained alongside T so that an expectation value can be read
+ * at the end (the magnetization study of Sec. 3.1 inserts one to measure M
+ * of the XY model).  Every half-step blocks it with the pure tensor in both
+ * places of the pair with the pure tensor's isometry, takes the mean of the
+ * two, and divides it by the pure tensor's n_k; after N half-steps
+ * Tr T_imp / Tr T is the mean of <O> over the 2^N sites.  It triples the
+ * contraction work of a half-step.
+ *
+ * trg_init_impure: the model's own observable, after trg_init_tensor and
+ *   before the first half-step (else TRG_ESTATE): Ising O = s; XY O =
+ *   cos(theta) (site factor (I_{div-1}(beta h) + I_{div+1}(beta h)) / 2);
+ *   Potts O = [s = 0].
+ * trg_init_impure_raw: any impure tensor (host, same shape as the initial
+ *   tensor, copied before return); it is divided by the same n0 as T.
+ * A later trg_init_tensor / _raw drops the impure tensor.
+ */
+int trg_init_impure(trg_ctx* ctx);
+int trg_init_impure_raw(trg_ctx* ctx, const double* Timp_host);
+
+/* <O> = Tr T_imp / Tr T of the current tensors (TRG_ESTATE without an impure
+ * tensor, TRG_ENUMERIC if Tr T <= 0). */
+int trg_expectation(trg_ctx* ctx, double* value_out);
+
+/*
  * Run `nsteps` directional blockings (half-steps), continuing the x/y
  * alternation of earlier calls (x first).  Each half-step: environment M of
  * two stacked tensors, isometry U = leading min(Dx^2, Dcut) eigenvectors of M,

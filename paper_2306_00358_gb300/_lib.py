@@ -84,6 +84,9 @@ SIGNATURES = {
     "trg_set_precision": (c_int, [c_void_p, c_int, c_int, c_int]),
     "trg_init_tensor": (c_int, [c_void_p, c_int, c_double, c_double, c_int]),
     "trg_init_tensor_raw": (c_int, [c_void_p, P_double, c_int, c_int, c_double]),
+    "trg_init_impure": (c_int, [c_void_p]),
+    "trg_init_impure_raw": (c_int, [c_void_p, P_double]),
+    "trg_expectation": (c_int, [c_void_p, P_double]),
     "trg_coarse_grain": (c_int, [c_void_p, c_int, c_int]),
     "trg_free_energy": (c_int, [c_void_p, P_double, P_double]),
     "trg_get_spectrum": (c_int, [c_void_p, c_int, P_double, c_int, P_int]),

@@ -147,31 +147,44 @@ static void half_step(Ctx& ctx, int dcut) {
         ctx.region_end(tok, 0.0, 0.0);
     }
 
-    // output O (dn, ry, dn, ry) of the x formulas
-    View4 out;
-    int64_t newDx, newDy;
-    if (xdir) {
-        newDx = dn; newDy = Dy;
-        ctx.ensure(ctx.Tnext, (size_t)(dn * Dy * dn * Dy) * sizeof(double));
-        out = contiguous_view(ctx.Tnext.as<double>(), dn, Dy, dn, Dy);
-    } else {
+    // output O (dn, ry, dn, ry) of the x formulas, written in place of the
+    // coarse tensor (Dx', Dy', Dx', Dy')
+    const int64_t newDx = xdir ? dn : Dx, newDy = xdir ? Dy : dn;
+    const int64_t n_out = newDx * newDy * newDx * newDy;
+    auto out_view = [&](double* base) {
+        if (xdir) return contiguous_view(base, dn, Dy, dn, Dy);
         // Txy = permute(O, (3, 0, 1, 2)) has shape (ry, dn, ry, dn) = (Dx, dn, Dx, dn)
-        newDx = Dx; newDy = dn;
-        ctx.ensure(ctx.Tnext, (size_t)(Dx * dn * Dx * dn) * sizeof(double));
-        View4 txy = contiguous_view(ctx.Tnext.as<double>(), Dx, dn, Dx, dn);
-        out.p = txy.p;
-        out.n[0] = dn; out.n[1] = ry; out.n[2] = dn; out.n[3] = ry;
-        out.s[0] = txy.s[1]; out.s[1] = txy.s[2]; out.s[2] = txy.s[3]; out.s[3] = txy.s[0];
+        View4 txy = contiguous_view(base, Dx, dn, Dx, dn), o;
+        o.p = txy.p;
+        o.n[0] = dn; o.n[1] = ry; o.n[2] = dn; o.n[3] = ry;
+        o.s[0] = txy.s[1]; o.s[1] = txy.s[2]; o.s[2] = txy.s[3]; o.s[3] = txy.s[0];
+        return o;
+    };
+    ctx.ensure(ctx.Tnext, (size_t)n_out * sizeof(double));
+    contract(ctx, r, r, ctx.U.as<double>(), dn, out_view(ctx.Tnext.as<double>()), precision);
+    if (ctx.have_impure) {
+        // the impurity in the upper and in the lower tensor of the pair, same
+        // isometry (from the pure environment), then the mean of the two
+        View4 ri = contiguous_view(ctx.Timp.as<double>(), Dx, Dy, Dx, Dy);
+        ri.n[0] = r.n[0]; ri.n[1] = r.n[1]; ri.n[2] = r.n[2]; ri.n[3] = r.n[3];
+        ri.s[0] = r.s[0]; ri.s[1] = r.s[1]; ri.s[2] = r.s[2]; ri.s[3] = r.s[3];
+        ctx.ensure(ctx.Timp_next, (size_t)n_out * sizeof(double));
+        ctx.ensure(ctx.Timp_tmp, (size_t)n_out * sizeof(double));
+        contract(ctx, ri, r, ctx.U.as<double>(), dn, out_view(ctx.Timp_next.as<double>()), precision);
+        contract(ctx, r, ri, ctx.U.as<double>(), dn, out_view(ctx.Timp_tmp.as<double>()), precision);
+        launch_mean2(ctx, ctx.Timp_next.as<double>(), ctx.Timp_tmp.as<double>(), n_out);
     }
-    contract(ctx, r, ctx.U.as<double>(), dn, out, precision);
     {
         const int tok = ctx.region_begin(TRG_PHASE_NORM);
-        launch_normalise(ctx, ctx.Tnext.as<double>(), newDx * newDy * newDx * newDy, k, false);
+        launch_normalise(ctx, ctx.Tnext.as<double>(), n_out, k, false);
+        // the impure tensor is divided by the same n_k
+        if (ctx.have_impure) launch_scale_by_last_norm(ctx, ctx.Timp_next.as<double>(), n_out);
         ctx.region_end(tok, 0.0, 0.0);
     }
     const int st = read_status(ctx);
     if (st & ST_BAD_NORM) fail(TRG_ENUMERIC, "non-positive or non-finite norm at half-step " + std::to_string(k));
     std::swap(ctx.T, ctx.Tnext);
+    if (ctx.have_impure) std::swap(ctx.Timp, ctx.Timp_next);
     ctx.Dx = (int)newDx;
     ctx.Dy = (int)newDy;
     ctx.steps = k;
@@ -182,6 +195,8 @@ static void reset_solve(Ctx& ctx) {
     // a solve depends on its own inputs only, whatever the context ran before
     ctx.eig_hint[0] = ctx.eig_hint[1] = Ctx::EigHint();
     ctx.have_tensor = false;
+    ctx.have_impure = false;
+    ctx.model = -1;
     ctx.steps = 0;
     ctx.spectra.clear();
     TRG_CUDA(cudaMemsetAsync(ctx.scal.p, 0, SC_COUNT * sizeof(double), ctx.stream));
@@ -297,7 +312,8 @@ int trg_destroy(trg_ctx* ctx) {
     cudaStreamSynchronize(ctx->stream);
     Ctx& c = *ctx;
     for (trg::Buf* b : {&c.T, &c.Tnext, &c.M, &c.U, &c.scal, &c.status, &c.ws, &c.envP, &c.envQ, &c.eig,
-                        &c.eig_small, &c.flags, &c.split_ws, &c.f64_partial, &c.cons_ef})
+                        &c.eig_small, &c.flags, &c.split_ws, &c.f64_partial, &c.cons_ef, &c.Timp, &c.Timp_next,
+                        &c.Timp_tmp})
         c.release(*b);
     for (auto& kv : c.tables) c.release(kv.second);
     c.tables.clear();
@@ -356,6 +372,7 @@ int trg_init_tensor(trg_ctx* ctx, int model, double beta, double h, int D0) {
         ctx->ensure(ctx->T, 16 * sizeof(double));
         trg::launch_init_ising(*ctx, ctx->T.as<double>(), beta, h);
         trg::finish_init(*ctx, 2, 2, beta);
+        ctx->model = TRG_ISING; ctx->d0 = 2; ctx->h_field = h;
     } else if (model == TRG_XY) {
         if (D0 < 1 || D0 % 2 == 0 || D0 > 41) return bad(ctx, TRG_EINVAL, "XY: D0 must be odd, 1..41");
         trg::reset_solve(*ctx);
@@ -363,6 +380,7 @@ int trg_init_tensor(trg_ctx* ctx, int model, double beta, double h, int D0) {
         ctx->ensure(ctx->T, n * sizeof(double));
         trg::launch_init_xy(*ctx, ctx->T.as<double>(), D0, beta, h);
         trg::finish_init(*ctx, D0, D0, beta);
+        ctx->model = TRG_XY; ctx->d0 = D0; ctx->h_field = h;
     } else if (model == TRG_POTTS) {
         if (D0 < 2 || D0 > 8) return bad(ctx, TRG_EINVAL, "Potts: D0 = q must be 2..8");
         trg::reset_solve(*ctx);
@@ -370,6 +388,7 @@ int trg_init_tensor(trg_ctx* ctx, int model, double beta, double h, int D0) {
         ctx->ensure(ctx->T, n * sizeof(double));
         trg::launch_init_potts(*ctx, ctx->T.as<double>(), D0, beta, h);
         trg::finish_init(*ctx, D0, D0, beta);
+        ctx->model = TRG_POTTS; ctx->d0 = D0; ctx->h_field = h;
     } else {
         return bad(ctx, TRG_EINVAL, "unknown model");
     }
@@ -389,6 +408,60 @@ int trg_init_tensor_raw(trg_ctx* ctx, const double* T_host, int Dx, int Dy, doub
     ctx->ensure(ctx->T, n * sizeof(double));
     TRG_CUDA(cudaMemcpyAsync(ctx->T.p, T_host, n * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
     trg::finish_init(*ctx, Dx, Dy, beta);
+    return TRG_OK;
+    TRG_GUARD_END(ctx)
+}
+
+int trg_init_impure(trg_ctx* ctx) {
+    if (!ctx) return TRG_EINVAL;
+    if (!ctx->have_tensor || ctx->steps != 0 || ctx->model < 0)
+        return bad(ctx, TRG_ESTATE, "init_impure needs a fresh trg_init_tensor (model tensor, no half-steps yet)");
+    TRG_GUARD_BEGIN
+    TRG_CUDA(cudaSetDevice(ctx->device));
+    const int d0 = ctx->d0;
+    const size_t n = (size_t)d0 * d0 * d0 * d0;
+    ctx->ensure(ctx->Timp, n * sizeof(double));
+    if (ctx->model == TRG_ISING) trg::launch_init_ising(*ctx, ctx->Timp.as<double>(), ctx->beta, ctx->h_field, 1);
+    else if (ctx->model == TRG_XY) trg::launch_init_xy(*ctx, ctx->Timp.as<double>(), d0, ctx->beta, ctx->h_field, 1);
+    else trg::launch_init_potts(*ctx, ctx->Timp.as<double>(), d0, ctx->beta, ctx->h_field, 1);
+    // the pure tensor was divided by n0: so is the impure one
+    trg::launch_scale_by_exp_neg(*ctx, ctx->Timp.as<double>(), (int64_t)n, ctx->scal.as<double>() + trg::SC_LN_N0);
+    ctx->have_impure = true;
+    return TRG_OK;
+    TRG_GUARD_END(ctx)
+}
+
+int trg_init_impure_raw(trg_ctx* ctx, const double* Timp_host) {
+    if (!ctx) return TRG_EINVAL;
+    if (!Timp_host) return bad(ctx, TRG_EINVAL, "init_impure_raw: no tensor");
+    if (!ctx->have_tensor || ctx->steps != 0)
+        return bad(ctx, TRG_ESTATE, "init_impure_raw needs a fresh initial tensor (no half-steps yet)");
+    TRG_GUARD_BEGIN
+    TRG_CUDA(cudaSetDevice(ctx->device));
+    const size_t n = (size_t)ctx->Dx * ctx->Dy * ctx->Dx * ctx->Dy;
+    ctx->ensure(ctx->Timp, n * sizeof(double));
+    TRG_CUDA(cudaMemcpyAsync(ctx->Timp.p, Timp_host, n * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+    trg::launch_scale_by_exp_neg(*ctx, ctx->Timp.as<double>(), (int64_t)n, ctx->scal.as<double>() + trg::SC_LN_N0);
+    TRG_CUDA(cudaStreamSynchronize(ctx->stream));   // the host buffer may go after return
+    ctx->have_impure = true;
+    return TRG_OK;
+    TRG_GUARD_END(ctx)
+}
+
+int trg_expectation(trg_ctx* ctx, double* value_out) {
+    if (!ctx) return TRG_EINVAL;
+    if (!value_out) return bad(ctx, TRG_EINVAL, "no output");
+    if (!ctx->have_tensor || !ctx->have_impure) return bad(ctx, TRG_ESTATE, "expectation without an impure tensor");
+    TRG_GUARD_BEGIN
+    TRG_CUDA(cudaSetDevice(ctx->device));
+    double* scal = ctx->scal.as<double>();
+    trg::launch_trace(*ctx, ctx->T.as<double>(), ctx->Dx, ctx->Dy, scal + trg::SC_TRACE);
+    trg::launch_trace_signed(*ctx, ctx->Timp.as<double>(), ctx->Dx, ctx->Dy, scal + trg::SC_TRACE_IMP);
+    double h[trg::SC_COUNT];
+    TRG_CUDA(cudaMemcpyAsync(h, scal, sizeof(h), cudaMemcpyDeviceToHost, ctx->stream));
+    TRG_CUDA(cudaStreamSynchronize(ctx->stream));
+    if (trg::read_status(*ctx) & trg::ST_BAD_TRACE) return bad(ctx, TRG_ENUMERIC, "non-positive trace");
+    *value_out = h[trg::SC_TRACE_IMP] / h[trg::SC_TRACE];
     return TRG_OK;
     TRG_GUARD_END(ctx)
 }
@@ -501,7 +574,7 @@ int trg_contract(trg_ctx* ctx, const double* t_dev, const double* U_dev, int Dx,
     TRG_CUDA(cudaSetDevice(ctx->device));
     trg::View4 t = trg::contiguous_view(const_cast<double*>(t_dev), Dx, Dy, Dx, Dy);
     trg::View4 o = trg::contiguous_view(Tx_dev, Dn, Dy, Dn, Dy);
-    trg::contract(*ctx, t, U_dev, Dn, o, ctx->cfg.precision);
+    trg::contract(*ctx, t, t, U_dev, Dn, o, ctx->cfg.precision);
     TRG_CUDA(cudaStreamSynchronize(ctx->stream));
     return TRG_OK;
     TRG_GUARD_END(ctx)

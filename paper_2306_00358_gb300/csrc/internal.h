@@ -65,6 +65,11 @@ struct Ctx {
     int steps = 0;
     double beta = 0.0;
     Buf T, Tnext;          // current / next site tensor
+    // impure tensor (an observable inserted at one site), blocked alongside T
+    bool have_impure = false;
+    int model = -1, d0 = 0;    // model of the last trg_init_tensor (-1 after a raw init)
+    double h_field = 0.0;
+    Buf Timp, Timp_next, Timp_tmp;
     Buf M;                 // environment
     Buf U;                 // isometry (n x Dn row-major)
     Buf scal;              // device scalars, see SC_* below
@@ -118,6 +123,7 @@ enum : int {
     SC_NORM = 2,      // last max|T| (as the bits of a non-negative double)
     SC_TRACE = 3,     // last trace
     SC_RES = 4,       // max Ritz residual / lambda_1 (subspace iteration)
+    SC_TRACE_IMP = 5, // last trace of the impure tensor
     SC_COUNT = 8
 };
 
@@ -183,15 +189,27 @@ std::vector<int64_t> build_table(const std::vector<std::pair<int64_t, int64_t>>&
 // ------------------------------------------------------ path pieces ----
 int precision_for_step(const Ctx& ctx, int step);
 void environment(Ctx& ctx, const View4& t, double* M, int precision);
-void contract(Ctx& ctx, const View4& t, const double* U, int64_t Dn, const View4& out, int precision);
+// Tx = U . top . bottom . U (the upper tensor of the blocked pair is `top`,
+// the lower one `bottom`; both the same tensor for the pure half-step).
+void contract(Ctx& ctx, const View4& top, const View4& bottom, const double* U, int64_t Dn, const View4& out,
+              int precision);
 // Returns Dn actually kept; lam (host) gets the kept eigenvalues.
 int isometry(Ctx& ctx, const double* M, int64_t n, int dcut, double* U, std::vector<double>& lam,
              int step, int precision);
 
 // Small kernels (small_kernels.cu)
-void launch_init_ising(Ctx& ctx, double* T, double beta, double h);
-void launch_init_xy(Ctx& ctx, double* T, int d0, double beta, double h);
-void launch_init_potts(Ctx& ctx, double* T, int q, double beta, double h);
+// impure = 1: the observable inserted (Ising s, XY cos(theta), Potts [s = 0])
+void launch_init_ising(Ctx& ctx, double* T, double beta, double h, int impure = 0);
+void launch_init_xy(Ctx& ctx, double* T, int d0, double beta, double h, int impure = 0);
+void launch_init_potts(Ctx& ctx, double* T, int q, double beta, double h, int impure = 0);
+// x *= exp(-scal[slot]) (the impure tensor takes the pure tensor's ln n0)
+void launch_scale_by_exp_neg(Ctx& ctx, double* x, int64_t n, const double* slot);
+// x *= 1 / (the norm in scal[SC_NORM]), the pure tensor's last n_k
+void launch_scale_by_last_norm(Ctx& ctx, double* x, int64_t n);
+// y = (y + z) / 2
+void launch_mean2(Ctx& ctx, double* y, const double* z, int64_t n);
+// Tr T into a slot without the positivity check (an observable's trace may be <= 0)
+void launch_trace_signed(Ctx& ctx, const double* T, int64_t Dx, int64_t Dy, double* slot);
 void launch_maxabs(Ctx& ctx, const double* x, int64_t n, double* slot_bits);
 void launch_normalise(Ctx& ctx, double* x, int64_t n, int step_weight_exp, bool initial);
 void launch_trace(Ctx& ctx, const double* T, int64_t Dx, int64_t Dy, double* slot);

@@ -120,9 +120,10 @@ void environment(Ctx& ctx, const View4& t, double* M, int precision) {
     }
 }
 
-// Tx[i,j,k,l] = sum U[a,b,i] t[b,j,d,c] t[a,c,e,l] U[e,d,k], in slices of j:
+// Tx[i,j,k,l] = sum U[a,b,i] t[b,j,d,c] t'[a,c,e,l] U[e,d,k], in slices of j
+// (t = top, t' = bottom of the blocked pair):
 //   X1[(jj,i,d),(c,a)] = sum_b U[a,b,i] t[b,j0+jj,d,c]          (D^6)
-//   X2[(jj,i,l),(e,d)] = sum_{c,a} X1[(jj,i,d),(c,a)] t[a,c,e,l]  (D^7)
+//   X2[(jj,i,l),(e,d)] = sum_{c,a} X1[(jj,i,d),(c,a)] t'[a,c,e,l] (D^7)
 //   O[i,j0+jj,k,l]     = sum_{e,d} X2[(jj,i,l),(e,d)] U[e,d,k]    (D^6)
 // The summed pair of each product is ordered with the producer's row index
 // fastest ((c,a) and (e,d)), so a producer warp, whose lanes are adjacent
@@ -130,9 +131,14 @@ void environment(Ctx& ctx, const View4& t, double* M, int precision) {
 // producer either records the exponent fields of its consumer's rows (the
 // consumer then skips the exponent pass over the D^5 intermediate) or, when
 // the bond dimensions tile (32, 64, 128), writes the consumer's slices.
-void contract(Ctx& ctx, const View4& t, const double* U, int64_t Dn, const View4& out, int precision) {
+void contract(Ctx& ctx, const View4& top, const View4& bottom, const double* U, int64_t Dn, const View4& out,
+              int precision) {
+    const View4& t = top;
+    if (bottom.n[0] != top.n[0] || bottom.n[1] != top.n[1] || bottom.n[2] != top.n[2] || bottom.n[3] != top.n[3])
+        fail(TRG_EINVAL, "contract: the two tensors of a pair differ in shape");
     const int64_t Dx = t.n[0], Dy = t.n[1];
     const int64_t* s = t.s;
+    const int64_t* sb = bottom.s;
     const int64_t* o = out.s;
     const int64_t DD = Dx * Dy;
     const bool split = precision == TRG_SPLIT_BF16;
@@ -214,7 +220,7 @@ void contract(Ctx& ctx, const View4& t, const double* U, int64_t Dn, const View4
             GemmDesc g;
             g.M = M2; g.N = DD; g.K = DD;
             g.A = gather(ctx, X1, {{jb * Dn * Dx, DD}}, {{DD, 1}});
-            g.B = gather(ctx, t.p, {{Dy, s[1]}, {Dx, s[0]}}, {{Dy, s[3]}, {Dx, s[2]}});
+            g.B = gather(ctx, bottom.p, {{Dy, sb[1]}, {Dx, sb[0]}}, {{Dy, sb[3]}, {Dx, sb[2]}});
             // consumer row of element ((jj,i,d),(l,e)) is (jj,i,l), its column e Dx + d
             g.cons_m = ctx.table({{jb * Dn, Dy}, {Dx, 0}});
             g.cons_n = ctx.table({{Dy, 1}, {Dx, 0}});

@@ -29,7 +29,8 @@ __device__ double bessel_i_series(int n, double x) {
 // Ising: T[i,j,k,l] = sum_s e^{beta h s} W[s,i] W[s,j] W[s,k] W[s,l],
 // W = B^(1/2), B = [[e^b, e^-b], [e^-b, e^b]] (s = +1, -1), from B's
 // eigenpairs 2cosh(b) on (1,1)/sqrt2 and 2sinh(b) on (1,-1)/sqrt2.
-__global__ void k_init_ising(double* T, double beta, double h) {
+// impure: the spin s inserted at the site (factor s in the sum).
+__global__ void k_init_ising(double* T, double beta, double h, int impure) {
     const int e = threadIdx.x;
     if (e >= 16) return;
     const int i = (e >> 3) & 1, j = (e >> 2) & 1, k = (e >> 1) & 1, l = e & 1;
@@ -39,14 +40,16 @@ __global__ void k_init_ising(double* T, double beta, double h) {
     double t = 0.0;
     for (int s = 0; s < 2; ++s) {
         const double spin = s == 0 ? 1.0 : -1.0;
-        t += exp(beta * h * spin) * w[s][i] * w[s][j] * w[s][k] * w[s][l];
+        t += (impure ? spin : 1.0) * exp(beta * h * spin) * w[s][i] * w[s][j] * w[s][k] * w[s][l];
     }
     T[e] = t;
 }
 
 // XY (character expansion, |n| <= nmax, index = n + nmax):
 // T[nl,nu,nr,nd] = prod sqrt(I_n(beta)) * I_{nl+nu-nr-nd}(beta h)
-__global__ void k_init_xy(double* T, int d0, double beta, double h) {
+// impure: cos(theta) inserted; cos = (e^{i theta} + e^{-i theta}) / 2 turns the
+// site factor into (I_{div-1}(beta h) + I_{div+1}(beta h)) / 2.
+__global__ void k_init_xy(double* T, int d0, double beta, double h, int impure) {
     const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     const int64_t tot = (int64_t)d0 * d0 * d0 * d0;
     if (e >= tot) return;
@@ -56,13 +59,17 @@ __global__ void k_init_xy(double* T, int d0, double beta, double h) {
     const int nl = il - nmax, nu = iu - nmax, nr = ir - nmax, nd = id - nmax;
     const double legs = sqrt(bessel_i_series(nl, beta)) * sqrt(bessel_i_series(nu, beta)) *
                         sqrt(bessel_i_series(nr, beta)) * sqrt(bessel_i_series(nd, beta));
-    T[e] = legs * bessel_i_series(nl + nu - nr - nd, beta * h);
+    const int div = nl + nu - nr - nd;
+    const double site = impure ? 0.5 * (bessel_i_series(div - 1, beta * h) + bessel_i_series(div + 1, beta * h))
+                               : bessel_i_series(div, beta * h);
+    T[e] = legs * site;
 }
 
 // q-state Potts (q <= 8): W = L L^T with W_ss' = e^beta (s = s'), 1 otherwise;
 // T[i,j,k,l] = sum_s e^{beta h [s=0]} L[s,i] L[s,j] L[s,k] L[s,l].
 // Each thread factors the small W itself (plain Cholesky, row by row).
-__global__ void k_init_potts(double* T, int q, double beta, double h) {
+// impure: [s = 0] inserted (only the s = 0 term).
+__global__ void k_init_potts(double* T, int q, double beta, double h, int impure) {
     const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     const int64_t tot = (int64_t)q * q * q * q;
     if (e >= tot) return;
@@ -78,7 +85,7 @@ __global__ void k_init_potts(double* T, int q, double beta, double h) {
     }
     const int l = (int)(e % q), k = (int)((e / q) % q), j = (int)((e / q / q) % q), i = (int)(e / q / q / q);
     double t = 0.0;
-    for (int s = 0; s < q; ++s) {
+    for (int s = 0; s < (impure ? 1 : q); ++s) {
         const double w = (s == 0) ? exp(beta * h) : 1.0;
         t += w * L[s][i] * L[s][j] * L[s][k] * L[s][l];
     }
@@ -129,6 +136,18 @@ __global__ void __launch_bounds__(256) k_scale_by_norm(double* __restrict__ x, i
     for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n; q += stride) x[q] *= inv;
 }
 
+// x *= exp(-v), v read from a device slot.
+__global__ void __launch_bounds__(256) k_scale_by_exp_neg(double* __restrict__ x, int64_t n, const double* v) {
+    const double f = exp(-*v);
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n; q += stride) x[q] *= f;
+}
+
+__global__ void __launch_bounds__(256) k_mean2(double* __restrict__ y, const double* __restrict__ z, int64_t n) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n; q += stride) y[q] = 0.5 * (y[q] + z[q]);
+}
+
 // lognorm += 2^-k ln n_k   (k = 0: ln n0 slot instead)
 __global__ void k_lognorm(double* scal, int k, int* status) {
     const double nk = __longlong_as_double((long long)*(const unsigned long long*)(scal + SC_NORM));
@@ -138,7 +157,8 @@ __global__ void k_lognorm(double* scal, int k, int* status) {
 }
 
 // Tr T = sum_{i,j} T[i, j, i, j]
-__global__ void __launch_bounds__(256) k_trace(const double* T, int64_t Dx, int64_t Dy, double* out, int* status) {
+__global__ void __launch_bounds__(256) k_trace(const double* T, int64_t Dx, int64_t Dy, double* out, int* status,
+                                               int check) {
     double s = 0.0;
     for (int64_t e = threadIdx.x; e < Dx * Dy; e += 256) {
         const int64_t i = e / Dy, j = e % Dy;
@@ -152,7 +172,7 @@ __global__ void __launch_bounds__(256) k_trace(const double* T, int64_t Dx, int6
         double t = 0.0;
         for (int w = 0; w < 8; ++w) t += red[w];
         *out = t;
-        if (!(t > 0.0) || !isfinite(t)) atomicOr(status, ST_BAD_TRACE);
+        if (check && (!(t > 0.0) || !isfinite(t))) atomicOr(status, ST_BAD_TRACE);
     }
 }
 
@@ -188,20 +208,20 @@ unsigned grid_for(const Ctx& ctx, int64_t n, int threads) {
 
 }  // namespace
 
-void launch_init_ising(Ctx& ctx, double* T, double beta, double h) {
-    k_init_ising<<<1, 32, 0, ctx.stream>>>(T, beta, h);
+void launch_init_ising(Ctx& ctx, double* T, double beta, double h, int impure) {
+    k_init_ising<<<1, 32, 0, ctx.stream>>>(T, beta, h, impure);
     TRG_LAUNCHED(ctx);
 }
 
-void launch_init_xy(Ctx& ctx, double* T, int d0, double beta, double h) {
+void launch_init_xy(Ctx& ctx, double* T, int d0, double beta, double h, int impure) {
     const int64_t tot = (int64_t)d0 * d0 * d0 * d0;
-    k_init_xy<<<(unsigned)((tot + 127) / 128), 128, 0, ctx.stream>>>(T, d0, beta, h);
+    k_init_xy<<<(unsigned)((tot + 127) / 128), 128, 0, ctx.stream>>>(T, d0, beta, h, impure);
     TRG_LAUNCHED(ctx);
 }
 
-void launch_init_potts(Ctx& ctx, double* T, int q, double beta, double h) {
+void launch_init_potts(Ctx& ctx, double* T, int q, double beta, double h, int impure) {
     const int64_t tot = (int64_t)q * q * q * q;
-    k_init_potts<<<(unsigned)((tot + 127) / 128), 128, 0, ctx.stream>>>(T, q, beta, h);
+    k_init_potts<<<(unsigned)((tot + 127) / 128), 128, 0, ctx.stream>>>(T, q, beta, h, impure);
     TRG_LAUNCHED(ctx);
 }
 
@@ -222,7 +242,28 @@ void launch_normalise(Ctx& ctx, double* x, int64_t n, int k, bool initial) {
 }
 
 void launch_trace(Ctx& ctx, const double* T, int64_t Dx, int64_t Dy, double* slot) {
-    k_trace<<<1, 256, 0, ctx.stream>>>(T, Dx, Dy, slot, ctx.status.as<int>());
+    k_trace<<<1, 256, 0, ctx.stream>>>(T, Dx, Dy, slot, ctx.status.as<int>(), 1);
+    TRG_LAUNCHED(ctx);
+}
+
+void launch_trace_signed(Ctx& ctx, const double* T, int64_t Dx, int64_t Dy, double* slot) {
+    k_trace<<<1, 256, 0, ctx.stream>>>(T, Dx, Dy, slot, ctx.status.as<int>(), 0);
+    TRG_LAUNCHED(ctx);
+}
+
+void launch_scale_by_exp_neg(Ctx& ctx, double* x, int64_t n, const double* slot) {
+    k_scale_by_exp_neg<<<grid_for(ctx, n, 256), 256, 0, ctx.stream>>>(x, n, slot);
+    TRG_LAUNCHED(ctx);
+}
+
+void launch_scale_by_last_norm(Ctx& ctx, double* x, int64_t n) {
+    k_scale_by_norm<<<grid_for(ctx, n, 256), 256, 0, ctx.stream>>>(
+        x, n, (const unsigned long long*)(ctx.scal.as<double>() + SC_NORM));
+    TRG_LAUNCHED(ctx);
+}
+
+void launch_mean2(Ctx& ctx, double* y, const double* z, int64_t n) {
+    k_mean2<<<grid_for(ctx, n, 256), 256, 0, ctx.stream>>>(y, z, n);
     TRG_LAUNCHED(ctx);
 }
 

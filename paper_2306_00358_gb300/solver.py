@@ -125,6 +125,22 @@ class Solver:
         self._check(self._lib.trg_init_tensor_raw(self._h, t.ctypes.data_as(_lib.P_double), t.shape[0],
                                                   t.shape[1], float(beta)), "trg_init_tensor_raw")
 
+    def init_impure(self, t_imp: np.ndarray | None = None):
+        """Insert the model's observable (Ising s, XY cos theta, Potts [s=0]),
+        or the given impure tensor, to be blocked alongside the pure one."""
+        if t_imp is None:
+            self._check(self._lib.trg_init_impure(self._h), "trg_init_impure")
+            return
+        t_imp = np.ascontiguousarray(t_imp, dtype=np.float64)
+        self._check(self._lib.trg_init_impure_raw(self._h, t_imp.ctypes.data_as(_lib.P_double)),
+                    "trg_init_impure_raw")
+
+    def expectation(self) -> float:
+        """<O> = Tr T_imp / Tr T of the current tensors."""
+        v = ctypes.c_double()
+        self._check(self._lib.trg_expectation(self._h, ctypes.byref(v)), "trg_expectation")
+        return v.value
+
     def coarse_grain(self, dcut: int, nsteps: int):
         self._check(self._lib.trg_coarse_grain(self._h, int(dcut), int(nsteps)), "trg_coarse_grain")
 

@@ -46,7 +46,51 @@ def run(name, model, beta, h, dcut, nsteps, trunc):
     return rec
 
 
+EXPECTATION_CASES = [
+    # name, model, beta, h, dcut, nsteps, trunc: impure tensor of the model's observable
+    ("ising_bc_d16_h1e-3_n20", "ising", exact.BETA_C, 1e-3, 16, 20, "paper"),
+    ("ising_b0.6_d16_h1e-10_n40", "ising", 0.6, 1e-10, 16, 40, "paper"),
+    ("xy_b1.0_d12_h0.05_n12", "xy", 1.0, 0.05, 12, 12, "multiplet"),
+    ("potts_b1.0_d12_h0.02_n16", "potts", 1.0, 0.02, 12, 16, "multiplet"),
+]
+
+
+def expectations():
+    """oracle_expectations.json: <O> = Tr T_imp / Tr T of truncated solves and
+    of untruncated small tori (with the enumerated value beside it)."""
+    out = {"solves": {}, "tori": {}}
+    for (name, model, beta, h, dcut, nsteps, trunc) in EXPECTATION_CASES:
+        print("oracle (impure):", name, flush=True)
+        s = hotrg.solve(models.initial_tensor(model, beta, h), beta, dcut, nsteps, trunc=trunc,
+                        impure=models.impure_tensor(model, beta, h))
+        out["solves"][name] = {"model": model, "beta": beta, "h": h, "dcut": dcut, "nsteps": nsteps, "trunc": trunc,
+                               "expectation": s.expectation, "f": s.f,
+                               "source": "oracle/hotrg.py solve(impure=...) (CPU FP64)"}
+    for nsteps in (2, 3, 4):
+        w, hh = exact.hotrg_block(nsteps)
+        out["tori"][f"ising_b0.44_h0.01_n{nsteps}"] = {
+            "model": "ising", "beta": 0.44, "h": 0.01, "nsteps": nsteps,
+            "expectation": exact.ising_magnetization_exact(w, hh, 0.44, 0.01)}
+    for nsteps in (1, 2):
+        w, hh = exact.hotrg_block(nsteps)
+        out["tori"][f"xy_b0.9_h0.1_n{nsteps}"] = {
+            "model": "xy", "beta": 0.9, "h": 0.1, "nsteps": nsteps,
+            "expectation": exact.xy_cos_exact(w, hh, 0.9, 0.1, 9)}
+    for nsteps in (2, 3):
+        w, hh = exact.hotrg_block(nsteps)
+        out["tori"][f"potts_b0.8_h0.05_n{nsteps}"] = {
+            "model": "potts", "beta": 0.8, "h": 0.05, "nsteps": nsteps,
+            "expectation": exact.potts_fraction0_exact(w, hh, 0.8, 0.05, 3)}
+    with open(os.path.join(HERE, "oracle_expectations.json"), "w") as fh:
+        json.dump(out, fh, indent=1)
+    print("wrote oracle_expectations.json")
+
+
 def main():
+    if "--expectations" in sys.argv:
+        expectations()
+        return
+    expectations()
     out = {}
     for case in CASES:
         print("oracle:", case[0], flush=True)
