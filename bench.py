@@ -63,6 +63,7 @@ def parse():
     ap.add_argument("--requests", type=int, default=200)
     ap.add_argument("--rate", type=float, default=2.0, help="serve: mean arrivals per second")
     ap.add_argument("--slots", type=int, default=16)
+    ap.add_argument("--policy", default="fifo", choices=["fifo", "shortest"], help="serve: admission order")
     ap.add_argument("--seed", type=int, default=1234)
     return ap.parse_args()
 
@@ -496,7 +497,8 @@ def run_serve(args):
                              precision="split", slices=args.slices,
                              trunc="multiplet" if model == "xy" else "paper"))
     gaps = rng.exponential(1.0 / args.rate, size=len(specs))
-    with sv.Server(0, slots=args.slots, hbm_budget_bytes=150 << 30, workspace_bytes=1 << 30) as s:
+    with sv.Server(0, slots=args.slots, hbm_budget_bytes=150 << 30, workspace_bytes=1 << 30,
+                   policy=args.policy) as s:
         t0 = time.perf_counter()
         tickets = []
         for spec, gap in zip(specs, gaps):
@@ -509,7 +511,8 @@ def run_serve(args):
     by_d = {}
     for spec, r in zip(specs, res):
         by_d.setdefault(spec.dcut, []).append(r["seconds_queued"] + r["seconds_run"])
-    print(json.dumps({"mode": "serve", "requests": len(specs), "rate_per_s": args.rate, "slots": args.slots,
+    print(json.dumps({"mode": "serve", "policy": args.policy, "requests": len(specs), "rate_per_s": args.rate,
+                      "slots": args.slots,
                       "ok": sum(r["status"] == 0 for r in res), "wall_s": wall,
                       "p50_latency_s": float(np.percentile(lat, 50)), "p99_latency_s": float(np.percentile(lat, 99)),
                       "solves_per_s": st["solves_per_s"], "peak_admitted_bytes": st["peak_bytes"],

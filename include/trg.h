@@ -299,7 +299,16 @@ typedef struct trg_server_config {
     size_t workspace_bytes;        /* contraction workspace per solve (default 1 GiB) */
     int dry_run;                   /* 1: no GPU work, slots sleep (tests of the scheduler) */
     double dry_run_seconds_per_step;
+    int policy;                    /* TRG_SERVE_FIFO (default) or TRG_SERVE_SHORTEST_FIRST */
+    double max_wait_s;             /* shortest-first: a request queued this long goes next
+                                      (no starvation); default 60 */
 } trg_server_config;
+
+/* Admission order.  FIFO: the oldest queued request starts when a slot is
+ * free and its memory fits.  SHORTEST_FIRST: among the queued requests whose
+ * memory fits, the one with the least estimated work (half-steps x Dcut^7,
+ * the D^7 product's share) starts, unless the oldest has waited max_wait_s. */
+enum { TRG_SERVE_FIFO = 0, TRG_SERVE_SHORTEST_FIRST = 1 };
 
 typedef struct trg_serve_stats {
     uint64_t submitted, completed, failed, cancelled, running, queued;

@@ -50,6 +50,7 @@ class trg_phase_stats(ctypes.Structure):
 
 PHASES = ("env", "eig", "x1", "x2", "x3", "norm", "mma")
 TRG_EAGAIN, TRG_ECANCELED = 8, 9
+TRG_SERVE_FIFO, TRG_SERVE_SHORTEST_FIRST = 0, 1
 TRG_DRY_RUN_FAIL_SEED = 0xFA17FA17
 
 
@@ -66,7 +67,8 @@ class trg_solve_result(ctypes.Structure):
 
 class trg_server_config(ctypes.Structure):
     _fields_ = [("slots", c_int), ("hbm_budget_bytes", c_size_t), ("workspace_bytes", c_size_t),
-                ("dry_run", c_int), ("dry_run_seconds_per_step", c_double)]
+                ("dry_run", c_int), ("dry_run_seconds_per_step", c_double), ("policy", c_int),
+                ("max_wait_s", c_double)]
 
 
 class trg_serve_stats(ctypes.Structure):

@@ -57,10 +57,17 @@ size_t estimate_bytes(const trg_solve_spec& s, size_t workspace_cap) {
     return (size_t)bytes;
 }
 
+// Estimated work of a solve: half-steps x D^7 (the D^7 product dominates).
+double estimate_work(const trg_solve_spec& s) {
+    const double d = std::max(1, s.Dcut);
+    return (double)std::max(1, s.nsteps) * d * d * d * d * d * d * d;
+}
+
 struct Request {
     uint64_t ticket = 0;
     trg_solve_spec spec{};
     size_t bytes = 0;
+    double work = 0.0;
     Clock::time_point t_submit, t_start, t_end;
     enum { QUEUED, RUNNING, DONE, CANCELLED } state = QUEUED;
     trg_solve_result result{};
@@ -148,16 +155,29 @@ void trg_server::worker_main(int slot) {
     if (!cfg.dry_run) cudaSetDevice(device);
     std::unique_lock<std::mutex> lk(mu);
     for (;;) {
-        // FIFO: the head of the queue starts when a slot is free (this one)
-        // and its memory fits the budget; requests behind it wait their turn
-        cv_work.wait(lk, [&] {
-            if (stopping) return true;
-            if (queue.empty()) return false;
-            return in_use + queue.front()->bytes <= cfg.hbm_budget_bytes;
-        });
+        // the request this slot takes (queue.end() while none may start)
+        auto pick = [&]() {
+            if (queue.empty()) return queue.end();
+            if (cfg.policy == TRG_SERVE_FIFO ||
+                secs(queue.front()->t_submit, Clock::now()) >= cfg.max_wait_s) {
+                // FIFO, or the oldest request has waited long enough: the head
+                // of the queue starts when its memory fits; the rest wait
+                return in_use + queue.front()->bytes <= cfg.hbm_budget_bytes ? queue.begin() : queue.end();
+            }
+            // shortest first among those that fit (the oldest of equal work)
+            auto best = queue.end();
+            for (auto it = queue.begin(); it != queue.end(); ++it)
+                if (in_use + (*it)->bytes <= cfg.hbm_budget_bytes && (best == queue.end() || (*it)->work < (*best)->work))
+                    best = it;
+            return best;
+        };
+        std::deque<Request*>::iterator it;
+        // waits are bounded so that the starvation guard is re-checked
+        while (!stopping && (it = pick()) == queue.end())
+            cv_work.wait_for(lk, std::chrono::milliseconds(100));
         if (stopping) break;
-        Request* r = queue.front();
-        queue.pop_front();
+        Request* r = *it;
+        queue.erase(it);
         r->state = Request::RUNNING;
         r->t_start = Clock::now();
         in_use += r->bytes;
@@ -214,6 +234,8 @@ int trg_server_config_default(trg_server_config* cfg) {
     cfg->workspace_bytes = (size_t)1 << 30;
     cfg->dry_run = 0;
     cfg->dry_run_seconds_per_step = 1e-3;
+    cfg->policy = TRG_SERVE_FIFO;
+    cfg->max_wait_s = 60.0;
     return TRG_OK;
 }
 
@@ -243,6 +265,8 @@ int trg_serve_create(trg_server** out, int device, const trg_server_config* cfg)
     if (cfg) c = *cfg;
     else trg_server_config_default(&c);
     if (c.slots < 1 || c.slots > 256 || c.hbm_budget_bytes == 0) return TRG_EINVAL;
+    if (c.policy != TRG_SERVE_FIFO && c.policy != TRG_SERVE_SHORTEST_FIRST) return TRG_EINVAL;
+    if (!(c.max_wait_s >= 0.0)) return TRG_EINVAL;
     if (c.workspace_bytes == 0) c.workspace_bytes = (size_t)1 << 30;
     if (!c.dry_run) {
         int ndev = 0;
@@ -277,6 +301,7 @@ int trg_serve_submit(trg_server* s, const trg_solve_spec* spec, uint64_t* ticket
     if (!r) return TRG_ENOMEM;
     r->spec = *spec;
     r->bytes = estimate_bytes(*spec, s->cfg.workspace_bytes);
+    r->work = estimate_work(*spec);
     if (r->bytes > s->cfg.hbm_budget_bytes) {   // could never be admitted
         delete r;
         return TRG_ENOMEM;

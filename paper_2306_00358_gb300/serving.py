@@ -40,10 +40,15 @@ def _result(r: _lib.trg_solve_result) -> dict:
             "seconds_run": r.seconds_run, "slot": r.slot}
 
 
+_POLICIES = {"fifo": _lib.TRG_SERVE_FIFO, "shortest": _lib.TRG_SERVE_SHORTEST_FIRST}
+
+
 def server_config(slots=8, hbm_budget_bytes=150 << 30, workspace_bytes=1 << 30, dry_run=False,
-                  dry_run_seconds_per_step=1e-3) -> _lib.trg_server_config:
+                  dry_run_seconds_per_step=1e-3, policy="fifo", max_wait_s=60.0) -> _lib.trg_server_config:
+    """policy "fifo" (arrival order) or "shortest" (least estimated work first,
+    unless the oldest request has waited max_wait_s)."""
     return _lib.trg_server_config(int(slots), int(hbm_budget_bytes), int(workspace_bytes), 1 if dry_run else 0,
-                                  float(dry_run_seconds_per_step))
+                                  float(dry_run_seconds_per_step), _POLICIES[policy], float(max_wait_s))
 
 
 def solve_bytes(spec: Spec, workspace_bytes: int = 0) -> int:

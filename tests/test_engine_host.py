@@ -123,3 +123,39 @@ def test_batch_run_returns_in_order():
     specs = [sv.Spec(dcut=16, nsteps=3 + i) for i in range(5)]
     res = sv.batch_run(specs, slots=3, hbm_budget_bytes=1 << 40, **DRY)
     assert [r["status"] for r in res] == [0] * 5
+
+
+def _finish_order(policy, **extra):
+    # one slot, busy with a blocker while a long and three short requests queue
+    with sv.Server(slots=1, hbm_budget_bytes=1 << 40, policy=policy, **DRY, **extra) as s:
+        # the blocker sleeps 0.2 s, far longer than the submissions below take
+        blocker = s.submit(sv.Spec(dcut=32, nsteps=250))
+        time.sleep(0.005)
+        long_t = s.submit(sv.Spec(dcut=48, nsteps=40))
+        shorts = [s.submit(sv.Spec(dcut=16, nsteps=5)) for _ in range(3)]
+        s.wait(blocker)
+        res = {t: s.wait(t) for t in [long_t] + shorts}
+    end = {t: r["seconds_queued"] + r["seconds_run"] for t, r in res.items()}
+    return long_t, shorts, end
+
+
+def test_shortest_first_lets_short_requests_pass():
+    long_t, shorts, end = _finish_order("shortest")
+    assert all(end[t] < end[long_t] for t in shorts)
+    long_t, shorts, end = _finish_order("fifo")
+    assert all(end[t] > end[long_t] for t in shorts)
+
+
+def test_shortest_first_does_not_starve_a_long_request():
+    # with max_wait_s = 0 the oldest request always goes first: FIFO again
+    long_t, shorts, end = _finish_order("shortest", max_wait_s=0.0)
+    assert all(end[t] > end[long_t] for t in shorts)
+
+
+def test_bad_policy_is_rejected():
+    c = sv.server_config(**DRY)
+    c.policy = 7
+    lib = _lib.load()
+    import ctypes
+    h = ctypes.c_void_p()
+    assert lib.trg_serve_create(ctypes.byref(h), 0, ctypes.byref(c)) == _lib.TRG_EINVAL
