@@ -50,6 +50,9 @@ def parse():
     ap.add_argument("--gemm", type=int, nargs=3, metavar=("M", "N", "K"), default=None,
                     help="micro-benchmark one split GEMM of this size instead of the half-step")
     ap.add_argument("--sweep", action="store_true", help="FP64 vs split solves over couplings (accuracy)")
+    ap.add_argument("--sweep-model", default="ising", choices=["ising", "xy"])
+    ap.add_argument("--sweep-steps", type=int, default=None, help="half-steps (default 40 Ising, 30 XY)")
+    ap.add_argument("--fp64-max-dcut", type=int, default=64, help="sweep: FP64 reference solves up to this Dcut")
     ap.add_argument("--betas", default=None)
     ap.add_argument("--fields", default=None)
     ap.add_argument("--dcuts", default=None)
@@ -301,7 +304,11 @@ def run_native(args):
     # end to end through the C ABI with host buffers
     e2e = None
     if not args.no_e2e:
-        t_host = s.tensor()
+        # the step's input in pinned host memory (copied there before timing)
+        t_np = s.tensor()
+        pinned = torch.empty(t_np.shape, dtype=torch.float64, pin_memory=True)
+        pinned.numpy()[...] = t_np
+        t_host = pinned.numpy()                    # shares the pinned buffer
         h2d = t_host.nbytes
         s2 = s
         torch.cuda.synchronize()
@@ -313,7 +320,8 @@ def run_native(args):
             f, _ = s2.free_energy()                # device -> host read of the result
         torch.cuda.synchronize()
         e2e_s = (time.perf_counter() - t0) / ne
-        e2e = {"value": e2e_s, "unit": "s/half-step", "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": 16 + 8}
+        e2e = {"value": e2e_s, "unit": "s/half-step", "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": 16 + 8,
+               "host_buffer": "pinned"}
 
     solve = None
     if not args.no_solve:
@@ -403,33 +411,43 @@ def run_sweep(args):
 
     from paper_2306_00358_gb300 import Solver
 
-    betas = [float(b) for b in args.betas.split(",")] if args.betas else [BETA_C, 0.40, 0.48]
-    fields = [float(h) for h in args.fields.split(",")] if args.fields else [0.0, 1e-3]
-    dcuts = [int(d) for d in args.dcuts.split(",")] if args.dcuts else [32, 48, 64]
+    xy = args.sweep_model == "xy"
+    # config 2 (Ising) or config 3 (XY, D0 = 9, multiplet truncation)
+    betas = [float(b) for b in args.betas.split(",")] if args.betas else \
+        ([0.9, 1.0, 1.1, 1.2] if xy else [BETA_C, 0.40, 0.48])
+    fields = [float(h) for h in args.fields.split(",")] if args.fields else ([0.0] if xy else [0.0, 1e-3])
+    dcuts = [int(d) for d in args.dcuts.split(",")] if args.dcuts else ([64, 96] if xy else [32, 48, 64])
+    nsteps = args.sweep_steps or (30 if xy else 40)
+    trunc = "multiplet" if xy else "paper"
     out = []
     for dcut in dcuts:
         for beta in betas:
             for h in fields:
-                rec = {"beta": beta, "h": h, "dcut": dcut}
-                for prec, slices in (("fp64", 4), ("split", args.slices)):
+                rec = {"model": args.sweep_model, "beta": beta, "h": h, "dcut": dcut, "half_steps": nsteps}
+                precs = [("split", args.slices)]
+                if dcut <= args.fp64_max_dcut:
+                    precs.insert(0, ("fp64", 4))
+                for prec, slices in precs:
                     torch.cuda.synchronize()
                     t0 = time.perf_counter()
-                    with Solver(0, precision=prec, split_slices=slices) as s:
-                        s.init_tensor("ising", beta, h)
-                        s.coarse_grain(dcut, 40)
+                    with Solver(0, precision=prec, split_slices=slices, trunc=trunc) as s:
+                        s.init_tensor(args.sweep_model, beta, h)
+                        s.coarse_grain(dcut, nsteps)
                         f, _ = s.free_energy()
                     rec[f"f_{prec}"] = f
                     rec[f"seconds_{prec}"] = time.perf_counter() - t0
-                rec["abs_df_split_fp64"] = abs(rec["f_split"] - rec["f_fp64"])
-                if h == 0.0:
+                if "f_fp64" in rec:
+                    rec["abs_df_split_fp64"] = abs(rec["f_split"] - rec["f_fp64"])
+                if h == 0.0 and not xy:
                     fe = onsager_f(beta)
                     rec["f_exact"] = fe
                     rec["rel_err_fp64"] = abs(rec["f_fp64"] - fe) / abs(fe)
                     rec["rel_err_split"] = abs(rec["f_split"] - fe) / abs(fe)
                 print(json.dumps(rec), flush=True)
                 out.append(rec)
-    print(json.dumps({"mode": "sweep", "slices": args.slices, "runs": len(out),
-                      "max_abs_df_split_fp64": max(r["abs_df_split_fp64"] for r in out)}), flush=True)
+    dfs = [r["abs_df_split_fp64"] for r in out if "abs_df_split_fp64" in r]
+    print(json.dumps({"mode": "sweep", "model": args.sweep_model, "slices": args.slices, "runs": len(out),
+                      "max_abs_df_split_fp64": max(dfs) if dfs else None}), flush=True)
 
 
 def _fp64_solve_seconds(dcut, nsteps=40, model="ising", beta=BETA_C, h=0.0):
