@@ -558,11 +558,29 @@ int isometry(Ctx& ctx, const double* M, int64_t n, int dcut, double* U, std::vec
         k_rand_cols<<<grid, 256, 0, ctx.stream>>>(Q, n, m, nullptr, seed, salt);
         TRG_LAUNCHED(ctx);
     }
-    // Y = M Q
+    // Y = M Q.  In split mode M is sliced once for all the products of this
+    // solve (each product then slices only the n x m block Q).
+    Gather gm;
+    gm.base = M; gm.off_r = ctx.table({{n, n}}); gm.off_c = ctx.table({{n, 1}}); gm.c_fast = true;
+    gm.c_identity = true;
+    const uint16_t* m_slices = nullptr;
+    const int* m_e = nullptr;
+    if (precision == TRG_SPLIT_BF16) {
+        const size_t sl = (size_t)ctx.cfg.split_slices * split_rows_padded(ctx, n) * split_k_padded(n) * 2;
+        const size_t eb = (size_t)split_rows_padded(ctx, n) * sizeof(int);
+        ctx.ensure(ctx.eig_slices, sl + eb + 256);
+        uint16_t* sp = ctx.eig_slices.as<uint16_t>();
+        int* ep = (int*)(ctx.eig_slices.as<uint8_t>() + ((sl + 255) & ~(size_t)255));
+        split_slice_operand(ctx, gm, n, n, sp, ep);
+        m_slices = sp;
+        m_e = ep;
+    }
     auto apply_m = [&]() {
         GemmDesc g;
         g.M = n; g.N = m; g.K = n;
-        g.A.base = M; g.A.off_r = ctx.table({{n, n}}); g.A.off_c = ctx.table({{n, 1}}); g.A.c_fast = true;
+        g.A = gm;
+        g.a_slices = m_slices;
+        g.a_e = m_e;
         g.B.base = Q; g.B.off_r = ctx.table({{n, 1}}); g.B.off_c = ctx.table({{m, n}}); g.B.c_fast = false;
         g.C = Y; g.c_m = ctx.table({{n, 1}}); g.c_n = ctx.table({{m, n}}); g.beta = 0.0;
         gemm(ctx, g, precision);

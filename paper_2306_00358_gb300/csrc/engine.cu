@@ -52,6 +52,7 @@ size_t estimate_bytes(const trg_solve_spec& s, size_t workspace_cap) {
         const double jb = std::max(1.0, std::floor(ws / std::max(1.0, 2 * D * D * D2 * 8)));
         const double rows_a = std::min(D, jb) * D * D + 128, rows_b = D2 + 128;
         bytes += (double)std::max(2, s.split_slices) * (rows_a + rows_b) * (D2 + 32) * 2 + (rows_a + rows_b) * 4;
+        bytes += (double)std::max(2, s.split_slices) * (D2 + 256) * (D2 + 32) * 2;   // M sliced for the isometry
     }
     bytes += 64.0 * 1024 * 1024;               // tables, scalars, allocator slack
     return (size_t)bytes;
@@ -215,7 +216,8 @@ namespace trg {
 void trim_buffers(Ctx& c) {
     cudaStreamSynchronize(c.stream);
     for (Buf* b : {&c.T, &c.Tnext, &c.M, &c.U, &c.ws, &c.envP, &c.envQ, &c.eig, &c.eig_small, &c.flags,
-                   &c.split_ws, &c.f64_partial, &c.cons_ef})
+                   &c.split_ws, &c.f64_partial, &c.cons_ef, &c.eig_slices, &c.Timp,
+                   &c.Timp_next, &c.Timp_tmp})
         c.release(*b);
     for (auto& kv : c.tables) c.release(kv.second);
     c.tables.clear();

@@ -85,6 +85,7 @@ struct Ctx {
     Buf split_ws;          // split GEMM: exponents and BF16 slices of both operands
     Buf f64_partial;       // FP64 GEMM: split-K partial sums
     Buf cons_ef;           // exponent fields recorded by a producing product (two halves)
+    Buf eig_slices;        // split mode: M sliced once per isometry solve
     std::map<std::string, Buf> tables;  // cached offset tables
 
     // ---- phase timing
@@ -136,6 +137,7 @@ struct Gather {
     const int64_t* off_r;   // row offsets   (A: m, B: k, C: m)
     const int64_t* off_c;   // col offsets   (A: k, B: n, C: n)
     bool c_fast;            // consecutive columns are adjacent in memory
+    bool c_identity = false;   // off_c[k] == k: every row is one contiguous run
 };
 struct GemmDesc {
     int64_t M, N, K;
@@ -179,6 +181,8 @@ struct GemmDesc {
 // K columns reads for its A operand (the fused hand-over writes this layout).
 int64_t split_rows_padded(const Ctx& ctx, int64_t M);
 int64_t split_k_padded(int64_t K);
+// Slice an A operand once for several split products (GemmDesc::a_slices / a_e).
+void split_slice_operand(Ctx& ctx, const Gather& A, int64_t M, int64_t K, uint16_t* slices, int* e);
 void gemm(Ctx& ctx, const GemmDesc& g, int precision);
 void gemm_f64(Ctx& ctx, const GemmDesc& g);
 

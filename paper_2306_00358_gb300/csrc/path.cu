@@ -56,6 +56,7 @@ static Gather gather(Ctx& ctx, const double* base, const Modes& rows, const Mode
     g.off_r = ctx.table(rows);
     g.off_c = ctx.table(cols);
     g.c_fast = unit_first_stride(cols);
+    g.c_identity = cols.size() == 1 && cols[0].second == 1;
     return g;
 }
 

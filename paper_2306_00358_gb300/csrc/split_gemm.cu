@@ -36,10 +36,11 @@
 // bounded: on expiry the kernel records ST_TIMEOUT and leaves its loops.
 //
 // A second instance runs each 256 x 128 tile on a CTA pair (cta_group::2):
-// each CTA stages its own 128 rows of A and half of B, the even CTA issues
-// the MMAs for both, and its barriers collect the loads and TMEM drains of
-// the pair.  It gives identical results; on this part it measured about 4 %
-// slower than the single-CTA kernel, so it is off by default (mma_pairs).
+// each CTA stages its own 128 rows of A and every other B slice in full (the
+// even CTA B0, B2, ..., the odd one B1, B3, ...), so every instruction is a
+// 256 x 256 x 16 product A_p [B_2b | B_2b+1] that drives both SMs; the even
+// CTA issues for both, and its barriers collect the loads and TMEM drains of
+// the pair (pair_ins_of).  Off by default (mma_pairs).
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
@@ -69,9 +70,12 @@ constexpr int SMEM_LIMIT = 232448;             // opt-in shared memory per block
 constexpr int BAR_BYTES = 512;                 // mbarriers, TMEM address, flags, row maxima
 
 // CG = CTAs per MMA (1, or a pair with cta_group::2).  A CTA stages its own
-// 128 rows of A and 128 / CG columns of B per slice and stage.
-__host__ __device__ constexpr int b_tile_bytes(int CG) { return TILE_BYTES / CG; }
-__host__ __device__ constexpr int stage_bytes_for(int S, int CG) { return S * (TILE_BYTES + b_tile_bytes(CG)); }
+// 128 rows of A (all S slices) and 128-row B slice tiles per stage.
+// B tiles a CTA stages per stage: all S (one CTA), or every other slice on a
+// pair (the even CTA B0, B2, ..., the odd one B1, B3, ...; for odd S the last
+// one is past the slice array and TMA fills it with zeros).
+__host__ __device__ constexpr int b_tiles(int S, int CG) { return CG == 1 ? S : (S + 1) / 2; }
+__host__ __device__ constexpr int stage_bytes_for(int S, int CG) { return (S + b_tiles(S, CG)) * TILE_BYTES; }
 __host__ __device__ constexpr int stages_for(int S, int CG) {
     return CG == 1 ? (S <= 4 ? 3 : 2)
                    : ((SMEM_LIMIT - 1024 - BAR_BYTES - STAGING_BYTES) / stage_bytes_for(S, CG) > 6
@@ -433,6 +437,56 @@ __host__ __device__ constexpr bool ins_cover_ok(int S) {
 }
 static_assert(ins_cover_ok(2) && ins_cover_ok(3) && ins_cover_ok(4) && ins_cover_ok(5), "slice product table");
 
+// The same for a CTA pair.  Entry b is the pair of B slices (2b, 2b+1) (the
+// even CTA holds 2b, the odd one 2b+1), always N = 256 across the pair
+// (each instruction drives both SMs for 128 x 256 x 16), so single products
+// are paired with one more: A1 B3 and A3 B1 (S = 4), A2 B3 and A4 B1 (S = 5)
+// go into R2 at p + q = S, beyond the truncation (more accurate, not less);
+// with S = 2, 3 the epilogue ignores R / R2 as it does for one CTA.
+__host__ __device__ constexpr int pair_ins_count(int S) { return S == 2 ? 2 : S == 3 ? 4 : S == 4 ? 6 : 9; }
+__host__ __device__ constexpr SliceIns pair_ins_of(int S, int t) {
+    return S == 2 ? (t == 0 ? SliceIns{0, 0, 1, 0, 0, 1} : SliceIns{1, 0, 1, 128, 2, 1})
+         : S == 3 ? (t == 0 ? SliceIns{0, 0, 1, 0, 0, 1}
+                   : t == 1 ? SliceIns{2, 0, 1, 256, 1, 1}
+                   : t == 2 ? SliceIns{1, 0, 1, 128, 2, 1}
+                            : SliceIns{0, 1, 1, 256, 2, 2})
+         : S == 4 ? (t == 0 ? SliceIns{0, 0, 1, 0, 0, 1}
+                   : t == 1 ? SliceIns{2, 0, 1, 256, 1, 1}
+                   : t == 2 ? SliceIns{1, 0, 1, 128, 2, 1}
+                   : t == 3 ? SliceIns{0, 1, 1, 256, 2, 2}
+                   : t == 4 ? SliceIns{1, 1, 1, 256, 2, 2}
+                            : SliceIns{3, 0, 1, 256, 2, 2})
+                  : (t == 0 ? SliceIns{0, 0, 1, 0, 0, 1}
+                   : t == 1 ? SliceIns{2, 0, 1, 256, 1, 1}
+                   : t == 2 ? SliceIns{1, 0, 1, 128, 2, 1}
+                   : t == 3 ? SliceIns{0, 1, 1, 256, 2, 2}
+                   : t == 4 ? SliceIns{1, 1, 1, 256, 2, 2}
+                   : t == 5 ? SliceIns{3, 0, 1, 256, 2, 2}
+                   : t == 6 ? SliceIns{2, 1, 1, 256, 2, 2}
+                   : t == 7 ? SliceIns{0, 2, 1, 256, 2, 2}
+                            : SliceIns{4, 0, 1, 256, 2, 2});
+}
+// Every product p + q < S exactly once; extra products only at p + q >= S
+// and never into ACC0 / ACC1 (columns < 256), whose sums must stay exact.
+__host__ __device__ constexpr bool pair_cover_ok(int S) {
+    int seen[6][6] = {};
+    for (int t = 0; t < pair_ins_count(S); ++t) {
+        const SliceIns in = pair_ins_of(S, t);
+        for (int h = 0; h < 2; ++h) {
+            const int p = in.a, q = 2 * in.b + h, col = in.col + 128 * h;
+            if (p >= S || q > S) return false;
+            if (q < S) seen[p][q] += 1;
+            if (p + q >= S && col < 256) return false;
+            if (col >= 512) return false;
+        }
+    }
+    for (int p = 0; p < S; ++p)
+        for (int q = 0; q < S; ++q)
+            if (p + q < S && seen[p][q] != 1) return false;
+    return true;
+}
+static_assert(pair_cover_ok(2) && pair_cover_ok(3) && pair_cover_ok(4) && pair_cover_ok(5), "pair product table");
+
 // Epilogue kinds: FP64 results stored through a staging tile (columns
 // adjacent in C), stored directly (rows adjacent in C), or the consumer's
 // slices (fused hand-over).  One kernel instance each keeps the register
@@ -444,9 +498,9 @@ __global__ void __launch_bounds__(THREADS, 1)
 k_split_mma(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, const MmaArgs g) {
     constexpr int STAGES = stages_for(S, CG);
     constexpr int STAGE_BYTES = stage_bytes_for(S, CG);
-    constexpr int B_TILE = b_tile_bytes(CG);
+    constexpr int B_TILE = TILE_BYTES;
+    constexpr int NB = b_tiles(S, CG);            // B slice tiles this CTA stages
     constexpr int TILE_M = BM * CG;                // output rows per tile (per CTA pair)
-    constexpr int B_ROWS = BN / CG;                // B columns this CTA stages
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint64_t* full = (uint64_t*)(smem + STAGES * STAGE_BYTES);
@@ -516,7 +570,7 @@ k_split_mma(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
             for (int tile = first_tile; tile < num_tiles && ok; tile += tile_step) {
                 int mb, nb;
                 tile_coords(tile, tiles_m, tiles_n, g.group_n, mb, nb);
-                const int arow = mb * TILE_M + (int)rank * BM, brow = nb * BN + (int)rank * B_ROWS;
+                const int arow = mb * TILE_M + (int)rank * BM, brow = nb * BN;
                 for (int kb = 0; kb < num_kb && ok; ++kb) {
                     ok = mbar_wait(&empty[stage], phase ^ 1, abort_flag, g.status);
                     if (!ok) break;
@@ -530,7 +584,11 @@ k_split_mma(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
                         } else {
                             const uint32_t bar = leader_full0 + (uint32_t)(stage * sizeof(uint64_t));
                             tma_load_2d_pair(st + p * TILE_BYTES, &tmA, kb * BK, p * g.Mp + arow, bar);
-                            tma_load_2d_pair(st + S * TILE_BYTES + p * B_TILE, &tmB, kb * BK, p * g.Np + brow, bar);
+                            if (p < NB) {
+                                // B slice 2p + rank (rows past the array read as zeros)
+                                tma_load_2d_pair(st + S * TILE_BYTES + p * B_TILE, &tmB, kb * BK,
+                                                 (2 * p + (int)rank) * g.Np + brow, bar);
+                            }
                         }
                     }
 #pragma unroll
@@ -574,23 +632,18 @@ k_split_mma(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
 #pragma unroll
                         for (int kk = 0; kk < BK / 16; ++kk) {
 #pragma unroll
-                            for (int t = 0; t < ins_count(S); ++t) {
-                                const SliceIns in = ins_of(S, t);
+                            for (int t = 0; t < (CG == 1 ? ins_count(S) : pair_ins_count(S)); ++t) {
+                                const SliceIns in = CG == 1 ? ins_of(S, t) : pair_ins_of(S, t);
                                 if (in.group != group) continue;
                                 uint32_t acc = 1u;
                                 if (in.flag == 0) acc = (chunk_start && kk == 0) ? 0u : 1u;
                                 if (in.flag == 1) acc = (kb == 0 && kk == 0) ? 0u : 1u;
                                 const uint64_t da = dbase + (uint64_t)((in.a * TILE_BYTES + kk * 32) >> 4);
                                 const uint64_t db = dbase + (uint64_t)((S * TILE_BYTES + in.b * B_TILE + kk * 32) >> 4);
-                                if constexpr (CG == 1) {
-                                    // B_q and B_q+1 are adjacent 128-row tiles: one N = 256 product
-                                    mma_bf16<CG>(tmem + in.col, da, db, in.wide ? IDESC_N256 : IDESC, acc);
-                                } else {
-                                    // a pair stages half of each B tile: two N = 128 products, same order
-                                    mma_bf16<CG>(tmem + in.col, da, db, IDESC, acc);
-                                    if (in.wide)
-                                        mma_bf16<CG>(tmem + in.col + 128, da, db + (uint64_t)(B_TILE >> 4), IDESC, acc);
-                                }
+                                // one CTA: B_q and B_q+1 are adjacent 128-row tiles, so a wide entry is
+                                // one N = 256 product; a pair: B tile b of the even CTA and the one at
+                                // the same place in the odd CTA, every entry 256 x 256
+                                mma_bf16<CG>(tmem + in.col, da, db, (CG == 2 || in.wide) ? IDESC_N256 : IDESC, acc);
                             }
                         }
                     };
@@ -968,6 +1021,72 @@ __global__ void __launch_bounds__(256) k_slice(const double* __restrict__ src, c
     }
 }
 
+// Slices of an operand whose rows are contiguous runs (src + off_r[r] + k):
+// a warp per row, four columns per lane per pass with 16-byte loads and
+// 8-byte stores of four BF16 per slice.  Same arithmetic as k_slice (the
+// slices are bit-identical), without the tile transpose through shared memory.
+template <int S>
+__global__ void __launch_bounds__(256) k_slice_contig(const double* __restrict__ src, const int64_t* __restrict__ off_r,
+                                                      int R, int K, int Rp, int Kp, const int* __restrict__ e_row,
+                                                      uint16_t* __restrict__ out) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int r = blockIdx.x * 8 + warp;
+    if (r >= Rp) return;
+    const size_t plane = (size_t)Rp * Kp;
+    uint16_t* orow = out + (size_t)r * Kp;
+    constexpr int F = 7 + 8 * (S - 1);
+    const bool real = r < R;
+    const double* row = real ? src + off_r[r] : nullptr;
+    const bool vec = real && ((reinterpret_cast<uintptr_t>(row) & 15) == 0);
+    const int ea = real ? e_row[r] : 0;
+    for (int k0 = lane * 4; k0 < Kp; k0 += 128) {
+        double v[4] = {0.0, 0.0, 0.0, 0.0};
+        if (real) {
+            if (vec && k0 + 3 < K) {
+                const double2 a = *reinterpret_cast<const double2*>(row + k0);
+                const double2 b = *reinterpret_cast<const double2*>(row + k0 + 2);
+                v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+            } else {
+#pragma unroll
+                for (int j = 0; j < 4; ++j)
+                    if (k0 + j < K) v[j] = row[k0 + j];
+            }
+        }
+        uint32_t pk[S][2];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const unsigned long long b = (unsigned long long)__double_as_longlong(v[j]);
+            const int ex = (int)((b >> 52) & 0x7FF);
+            long long X = 0;
+            if (ex) {
+                const int shift = 52 + 1023 + ea - ex - F;     // >= 53 - F > 0
+                if (shift < 63) {
+                    const unsigned long long m53 = (b & ((1ull << 52) - 1)) | (1ull << 52);
+                    X = (long long)((m53 + (1ull << (shift - 1))) >> shift);
+                    if (b >> 63) X = -X;
+                }
+            }
+            int d[S];
+#pragma unroll
+            for (int p = S - 1; p >= 1; --p) {
+                const int lo = (int)(((X + 128) & 255) - 128);
+                d[p] = lo;
+                X = (X - lo) >> 8;
+            }
+            d[0] = (int)X;
+#pragma unroll
+            for (int p = 0; p < S; ++p) {
+                const float f = (__int_as_float(0x4B400000 + d[p]) - 12582912.0f) * __int_as_float((127 - 8 * p) << 23);
+                const uint32_t hb = __float_as_uint(f) >> 16;
+                if (j & 1) pk[p][j >> 1] |= hb << 16;
+                else pk[p][j >> 1] = hb;
+            }
+        }
+#pragma unroll
+        for (int p = 0; p < S; ++p) *reinterpret_cast<uint2*>(orow + p * plane + k0) = make_uint2(pk[p][0], pk[p][1]);
+    }
+}
+
 // ------------------------------------------------------------- host side ---
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
     static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
@@ -1092,6 +1211,11 @@ void launch_mma(Ctx& ctx, const CUtensorMap& ta, const CUtensorMap& tb, const Mm
 
 template <int S>
 void launch_slice(Ctx& ctx, const Gather& g, int R, int K, int Rp, int Kp, const int* e, uint16_t* out) {
+    if (g.c_identity) {
+        k_slice_contig<S><<<(unsigned)((Rp + 7) / 8), 256, 0, ctx.stream>>>(g.base, g.off_r, R, K, Rp, Kp, e, out);
+        TRG_LAUNCHED(ctx);
+        return;
+    }
     dim3 grid((unsigned)((Kp + SL_K - 1) / SL_K), (unsigned)((Rp + SL_R - 1) / SL_R));
     k_slice<S><<<grid, 256, 0, ctx.stream>>>(g.base, g.off_r, g.off_c, R, K, Rp, Kp, g.c_fast ? 1 : 0, e, out);
     TRG_LAUNCHED(ctx);
@@ -1114,7 +1238,25 @@ static Gather transpose_gather(const Gather& b, const int64_t* off_k, const int6
     t.off_r = off_n;
     t.off_c = off_k;
     t.c_fast = false;
+    t.c_identity = false;
     return t;
+}
+
+// Exponents and BF16 slices of an A operand in the layout a split product
+// reads (rows padded per split_rows_padded, K per split_k_padded), for a
+// caller that reuses one A across several products.
+void split_slice_operand(Ctx& ctx, const Gather& A, int64_t M, int64_t K, uint16_t* slices, int* e) {
+    const int S = ctx.cfg.split_slices;
+    const int Mi = (int)M, Ki = (int)std::max<int64_t>(K, 1);
+    const int Mp = (int)split_rows_padded(ctx, M), Kp = (int)split_k_padded(K);
+    row_exponents(ctx, A, Mi, Ki, e);
+    switch (S) {
+        case 2: launch_slice<2>(ctx, A, Mi, Ki, Mp, Kp, e, slices); break;
+        case 3: launch_slice<3>(ctx, A, Mi, Ki, Mp, Kp, e, slices); break;
+        case 4: launch_slice<4>(ctx, A, Mi, Ki, Mp, Kp, e, slices); break;
+        case 5: launch_slice<5>(ctx, A, Mi, Ki, Mp, Kp, e, slices); break;
+        default: fail(TRG_EINVAL, "split_slices must be 2..5");
+    }
 }
 
 int64_t split_rows_padded(const Ctx& ctx, int64_t M) {
@@ -1172,7 +1314,7 @@ void gemm_split(Ctx& ctx, const GemmDesc& d) {
         default: fail(TRG_EINVAL, "split_slices must be 2..5");
     }
     const CUtensorMap ta = make_map(sa, S * Mp, Kp);
-    const CUtensorMap tb = make_map(sb, S * Np, Kp, BN / CG);
+    const CUtensorMap tb = make_map(sb, S * Np, Kp);
     MmaArgs a;
     a.M = M; a.N = N; a.Kp = Kp; a.Mp = Mp; a.Np = Np; a.S = S;
     a.ea = ea; a.eb = eb; a.C = d.C; a.c_m = d.c_m; a.c_n = d.c_n;
