@@ -13,6 +13,12 @@ ORACLE / TEST INFRASTRUCTURE ONLY.
       k = 2 sinh(2b) / cosh^2(2b)  (= 4 kappa);
     - the double-integral form
       -beta f = ln 2 + (1/8pi^2) int int ln[cosh^2(2b) - sinh(2b)(cos t1 + cos t2)].
+* Baxter's free energy of the q-state Potts model (weights e^{K [s = s']})
+  at its self-dual critical point e^{K_c} = 1 + sqrt(q), 0 < q < 4
+  (Baxter 1973; Baxter, Exactly Solved Models, sec. 12.5):
+      ln Z / V = (1/2) ln q + 2 int_0^inf sinh((pi - mu) x) tanh(mu x) / (x sinh(pi x)) dx,
+      sqrt(q) = 2 cos(mu).
+  It reduces to 2 ln 2 at q = 1 and to Onsager's value plus K_c at q = 2.
 * Brute-force partition functions of small periodic lattices: Ising by
   enumerating spins, XY by enumerating bond charges of the character
   expansion.  Bonds: every site couples to its right and its upper
@@ -175,6 +181,28 @@ def onsager_yang_magnetization(beta: float) -> float:
     if beta <= BETA_C:
         return 0.0
     return (1.0 - math.sinh(2.0 * beta) ** -4) ** 0.125
+
+
+def potts_critical_lnz(q: float) -> float:
+    """ln Z / V of the q-state Potts model at its critical point
+    T_c = 1 / ln(1 + sqrt(q)) (Sec. 3.3), infinite lattice, 0 < q < 4:
+    Baxter's closed form, the integral evaluated by adaptive quadrature with
+    sinh((pi - mu) x) / sinh(pi x) written as decaying exponentials."""
+    from scipy.integrate import quad
+
+    if not 0.0 < q < 4.0:
+        raise ValueError("the closed form holds for 0 < q < 4")
+    mu = math.acos(math.sqrt(q) / 2.0)
+
+    def integrand(x: float) -> float:
+        if x == 0.0:
+            return mu * (math.pi - mu) / math.pi   # limit x -> 0
+        ratio = math.exp(-mu * x) * (-math.expm1(-2.0 * (math.pi - mu) * x)) / (-math.expm1(-2.0 * math.pi * x))
+        return ratio * math.tanh(mu * x) / x
+
+    # the integrand decays like exp(-mu x) / x: nothing beyond x = 80 / mu counts
+    val, _ = quad(integrand, 0.0, 80.0 / mu, limit=2000, epsabs=1e-15, epsrel=1e-13)
+    return 0.5 * math.log(q) + 2.0 * val
 
 
 def potts_lnz_exact(width: int, height: int, beta: float, h: float = 0.0, q: int = 3) -> float:

@@ -186,6 +186,19 @@ def test_potts_enumeration_known_cases():
     assert exact.potts_lnz_exact(2, 2, beta, q=2) == pytest.approx(ref, abs=1e-12)
 
 
+def test_potts_critical_closed_form_special_cases():
+    # q = 1: every configuration weighs e^{2 K_c} per site, K_c = ln 2
+    assert exact.potts_critical_lnz(1.0) == pytest.approx(2 * math.log(2), abs=1e-13)
+    # q = 2: Ising at K = K_c / 2 (Onsager's integral form) plus K_c per site
+    kc = math.log(1 + math.sqrt(2))
+    assert exact.potts_critical_lnz(2.0) == pytest.approx(exact.onsager_integral(kc / 2) + kc, abs=1e-13)
+    # weights >= 1 bound ln Z / V from below by ln q, and the Peierls-type
+    # bound ln Z / V <= ln q + 2 K_c from above
+    for q in (1.5, 2.5, 3.0, 3.5):
+        kc = math.log(1 + math.sqrt(q))
+        assert math.log(q) < exact.potts_critical_lnz(q) < math.log(q) + 2 * kc
+
+
 def test_impure_tensors_reduce_to_pure_ones():
     # inserting O = 1 gives the pure tensor: Ising s = +-1 splits it in two
     # signed halves, Potts [s = 0] is one of the q terms, and the XY site

@@ -178,6 +178,15 @@ def test_potts_q2_is_ising_onsager():
     assert abs(sol.lnz_per_site - ref) <= 1e-9
 
 
+def test_potts_q3_at_tc_approaches_baxter():
+    # Sec. 3.3: q = 3 at T_c = 1 / ln(1 + sqrt 3) on a 2^20 x 2^20 lattice;
+    # truncated HOTRG at Dcut = 16 lies within 1e-4 of Baxter's
+    # infinite-lattice value (the finite-size shift is of order L^-2)
+    beta = math.log(1 + math.sqrt(3))
+    sol = hotrg.solve(models.potts_tensor(beta, 0.0, 3), beta, 16, 40)
+    assert abs(sol.lnz_per_site - exact.potts_critical_lnz(3)) <= 1e-4
+
+
 # ------------------------------------------------ impure tensors (observables) ---
 @pytest.mark.parametrize("nsteps", [2, 3, 4])
 @pytest.mark.parametrize("beta,h", [(0.44, 0.01), (0.3, -0.25), (0.6, 0.0)])
