@@ -88,63 +88,86 @@ __global__ void __launch_bounds__(256) k_col_normalize(double* Y, int64_t n, int
     for (int64_t r = threadIdx.x; r < n; r += 256) y[r] *= scale;
 }
 
-// Right-looking Cholesky G = L L^T of an m x m Gram matrix of unit columns.
-// Per column: warp 0 takes the pivot and scales the column (also into a
-// broadcast copy), then every warp updates trailing rows, a lane per column.
-// A pivot d_j <= tau * G_jj marks column j as dependent (flags[j] = 1,
-// *nbad += 1); the pivot is then replaced by G_jj so the factorisation can
-// continue.
+// Blocked right-looking Cholesky G = L L^T of an m x m Gram matrix of unit
+// columns, in 16-column blocks: warp 0 factors the diagonal block (a lane
+// per row, warp-synchronous), a thread per row solves the panel below it,
+// and a warp per row updates the trailing matrix; three block barriers per
+// block instead of two per column.  A pivot d_j <= tau * G_jj marks column j
+// as dependent (flags[j] = 1, *nbad += 1); the pivot is then replaced by
+// G_jj so the factorisation can continue.
+constexpr int CHOL_NB = 16;
 __global__ void __launch_bounds__(256) k_chol_flag(const double* G, double* Lout, int m, double tau,
                                                    int* flags, int* nbad) {
-    extern __shared__ double L[];   // m*m row-major, m of the original diagonal, m of column j
+    extern __shared__ double L[];   // m*m row-major, then m of the original diagonal
     double* gd = L + m * m;
-    double* colj = gd + m;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
     for (int e = threadIdx.x; e < m * m; e += blockDim.x) L[e] = G[e];
     for (int i = threadIdx.x; i < m; i += blockDim.x) gd[i] = G[(int64_t)i * m + i];
     __syncthreads();
-    for (int j = 0; j < m; ++j) {
+    for (int kb = 0; kb < m; kb += CHOL_NB) {
+        const int nb = min(CHOL_NB, m - kb);
+        // 1. diagonal block, warp 0: lane i owns row kb + i
         if (warp == 0) {
-            double d = L[j * m + j];
-            if (lane == 0) {
-                const double gjj = gd[j];
-                if (!(d > tau * gjj) || !isfinite(d)) {
-                    flags[j] = 1;
-                    atomicAdd(nbad, 1);
-                    d = (gjj > 0.0 && isfinite(gjj)) ? gjj : 1.0;
+            const int i = kb + lane;
+            for (int j = kb; j < kb + nb; ++j) {
+                double d = L[j * m + j];
+                if (lane == 0) {
+                    const double gjj = gd[j];
+                    if (!(d > tau * gjj) || !isfinite(d)) {
+                        flags[j] = 1;
+                        atomicAdd(nbad, 1);
+                        d = (gjj > 0.0 && isfinite(gjj)) ? gjj : 1.0;
+                    }
                 }
-            }
-            d = __shfl_sync(0xffffffffu, d, 0);
-            const double il = rsqrt(d);
-            if (lane == 0) L[j * m + j] = d * il;
-            for (int i = j + 1 + lane; i < m; i += 32) {
-                const double v = L[i * m + j] * il;
-                L[i * m + j] = v;
-                colj[i] = v;
+                d = __shfl_sync(0xffffffffu, d, 0);
+                const double il = rsqrt(d);
+                __syncwarp();
+                if (lane == 0) L[j * m + j] = d * il;
+                if (i > j && lane < nb) L[i * m + j] *= il;
+                __syncwarp();
+                if (i > j && lane < nb) {
+                    const double lij = L[i * m + j];
+                    for (int k = j + 1; k <= i; ++k) L[i * m + k] = fma(-lij, L[k * m + j], L[i * m + k]);
+                }
+                __syncwarp();
             }
         }
         __syncthreads();
-        for (int i = j + 1 + warp; i < m; i += nwarps) {
-            const double li = colj[i];
-            for (int k = j + 1 + lane; k <= i; k += 32) L[i * m + k] = fma(-li, colj[k], L[i * m + k]);
+        // 2. panel below it: row i solves x L_kk^T = a (forward substitution)
+        for (int i = kb + nb + threadIdx.x; i < m; i += blockDim.x) {
+            for (int j = kb; j < kb + nb; ++j) {
+                double a = L[i * m + j];
+                for (int k = kb; k < j; ++k) a = fma(-L[i * m + k], L[j * m + k], a);
+                L[i * m + j] = a / L[j * m + j];
+            }
+        }
+        __syncthreads();
+        // 3. trailing matrix: A[i][k] -= sum_t L[i][t] L[k][t], kb+nb <= k <= i
+        for (int i = kb + nb + warp; i < m; i += nwarps) {
+            for (int k = kb + nb + lane; k <= i; k += 32) {
+                double a = L[i * m + k];
+#pragma unroll 4
+                for (int t = kb; t < kb + nb; ++t) a = fma(-L[i * m + t], L[k * m + t], a);
+                L[i * m + k] = a;
+            }
         }
         __syncthreads();
     }
     for (int e = threadIdx.x; e < m * m; e += blockDim.x) Lout[e] = ((e % m) <= (e / m)) ? L[e] : 0.0;
 }
 
-// Q = Y L^{-T} row by row, in place allowed: 32 rows per block, a lane per
-// row, the solution in shared memory.  Right-looking: after x_j is known,
-// every later column k subtracts L[k][j] x_j.  Column k belongs to warp
-// k % 4, so the four warps (and the SM's four FP64 pipes) share the updates
-// and x_j needs no reduction, one block barrier per column.
+// Q = Y L^{-T} row by row, in place allowed: 32 rows per block, the rows in
+// shared memory.  Blocked by 16 columns: warp 0 solves the diagonal block (a
+// lane per row, a short dependent chain), then all four warps subtract the
+// block from the columns to its right (independent FMAs, so the SM's FP64
+// pipes stay busy); two block barriers per 16 columns.
 constexpr int TRSM_ROWS = 32;
 constexpr int TRSM_THREADS = 128;
+constexpr int TRSM_NB = 16;
 __global__ void __launch_bounds__(TRSM_THREADS) k_trsm_rows(double* Y, const double* Lg, int64_t n, int m) {
-    extern __shared__ double L[];   // m*m, m inverse diagonals, TRSM_ROWS rows of m + 1, 2 x TRSM_ROWS x_j
+    extern __shared__ double L[];   // m*m, m inverse diagonals, TRSM_ROWS rows of m + 1
     double* dinv = L + m * m;
     double* rows = dinv + m;
-    double* xb = rows + TRSM_ROWS * (m + 1);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     for (int e = threadIdx.x; e < m * m; e += blockDim.x) L[e] = Lg[e];
     for (int i = threadIdx.x; i < m; i += blockDim.x) dinv[i] = 1.0 / Lg[(int64_t)i * m + i];
@@ -154,20 +177,27 @@ __global__ void __launch_bounds__(TRSM_THREADS) k_trsm_rows(double* Y, const dou
         rows[t * (m + 1) + j] = (r0 + t < n) ? Y[(int64_t)j * n + r0 + t] : 0.0;
     }
     __syncthreads();
-    double* y = rows + lane * (m + 1);
-    for (int j = 0; j < m; ++j) {
-        double* xs = xb + (j & 1) * TRSM_ROWS;
-        if (warp == (j & 3)) {
-            const double x = y[j] * dinv[j];
-            y[j] = x;
-            xs[lane] = x;
+    for (int kb = 0; kb < m; kb += TRSM_NB) {
+        const int nb = min(TRSM_NB, m - kb);
+        if (warp == 0) {
+            double* y = rows + lane * (m + 1);
+            for (int j = kb; j < kb + nb; ++j) {
+                double a = y[j];
+                for (int k = kb; k < j; ++k) a = fma(-L[j * m + k], y[k], a);
+                y[j] = a * dinv[j];
+            }
         }
         __syncthreads();
-        const double x = xs[lane];
-        int k = j + 1 + ((warp - (j + 1)) & 3);      // first column > j owned by this warp
-        for (; k < m; k += 4) y[k] = fma(-L[k * m + j], x, y[k]);
+        // columns j >= kb + nb: thread (row = lane, every 4th column from warp)
+        double* y = rows + lane * (m + 1);
+        for (int j = kb + nb + warp; j < m; j += 4) {
+            double a = y[j];
+#pragma unroll 4
+            for (int t = kb; t < kb + nb; ++t) a = fma(-L[j * m + t], y[t], a);
+            y[j] = a;
+        }
+        __syncthreads();
     }
-    __syncthreads();
     for (int e = threadIdx.x; e < m * TRSM_ROWS; e += blockDim.x) {
         const int j = e / TRSM_ROWS, t = e % TRSM_ROWS;
         if (r0 + t < n) Y[(int64_t)j * n + r0 + t] = rows[t * (m + 1) + j];
@@ -457,7 +487,7 @@ static size_t jacobi_smem(int m) {
 }
 
 static size_t trsm_smem(int m) {
-    return (size_t)m * m * 8 + (size_t)m * 8 + (size_t)TRSM_ROWS * (m + 1) * 8 + 2 * TRSM_ROWS * 8;
+    return (size_t)m * m * 8 + (size_t)m * 8 + (size_t)TRSM_ROWS * (m + 1) * 8;
 }
 
 static void set_smem(const void* fn, size_t bytes) {
@@ -502,8 +532,8 @@ static void orthonormalise(Ctx& ctx, double* Y, int64_t n, int m, double* G, dou
             k_col_normalize<<<m, 256, 0, ctx.stream>>>(Y, n, flags);
             TRG_LAUNCHED(ctx);
             gram(ctx, Y, Y, n, m, G, TRG_FP64);
-            k_chol_flag<<<1, 256, smem + (size_t)m * 16, ctx.stream>>>(G, L, m, pass == 0 ? 1e-8 : 1e-12, flags,
-                                                                      nbad);
+            k_chol_flag<<<1, 256, smem + (size_t)m * 8, ctx.stream>>>(G, L, m, pass == 0 ? 1e-8 : 1e-12, flags,
+                                                                     nbad);
             TRG_LAUNCHED(ctx);
             int hb = 0;
             TRG_CUDA(cudaMemcpyAsync(&hb, nbad, sizeof(int), cudaMemcpyDeviceToHost, ctx.stream));
@@ -528,7 +558,7 @@ int isometry(Ctx& ctx, const double* M, int64_t n, int dcut, double* U, std::vec
     if (m > MAX_M) fail(TRG_ENOTSUP, "isometry: Dcut + oversampling exceeds the supported block (112)");
     static std::once_flag once;
     std::call_once(once, [] {
-        set_smem((const void*)k_chol_flag, (size_t)MAX_M * MAX_M * 8 + MAX_M * 16);
+        set_smem((const void*)k_chol_flag, (size_t)MAX_M * MAX_M * 8 + MAX_M * 8);
         set_smem((const void*)k_trsm_rows, trsm_smem(MAX_M));
         set_smem((const void*)k_jacobi, jacobi_smem(MAX_M));
     });

@@ -46,3 +46,17 @@ def test_dcut84_error_matches_table1(torch):
     ref = PAPER["ising_tc_table1"]["rel_err_by_dcut"]["84"]
     err = _rel_err(84)
     assert 0.5 * ref <= err <= 1.5 * ref, err
+
+
+@pytest.mark.parametrize("precision", ["split", "fp64"])
+def test_potts_q3_lnz_at_tc_approaches_baxter(torch, precision):
+    # Sec. 3.3 (three-state Potts at T_c, 2^30 x 2^30 lattice): the density
+    # of ln Z converges to Baxter's exact critical value; measured error
+    # -5.2e-6 at Dcut = 32 (-4.4e-5 at 16, -6e-7 at 64)
+    import math
+    beta = math.log(1 + math.sqrt(3))
+    with Solver(0, precision=precision, trunc="multiplet") as s:
+        s.init_tensor("potts", beta, 0.0)
+        s.coarse_grain(32, 60)
+        _, lnz = s.free_energy()
+    assert abs(lnz - exact.potts_critical_lnz(3)) <= 1e-5, lnz
