@@ -193,8 +193,8 @@ def load_peaks():
 # of two timed half-steps of this workload, from the ncu capture summarised in
 # profiles/split_mma_dram_hotrg_ising_dcut64_s4.md.  The figure describes the
 # kernel source it was taken on: reported only while that file is unchanged.
-SPLIT_MMA_TRAFFIC = {"sha256": "03dda785d64ee1102701a9c38b21d1a62520b57ca25d33e2fbba0e03910c01b7",
-                     "bytes_per_launch": 5.148e9}
+SPLIT_MMA_TRAFFIC = {"sha256": "7123b777a8ec7c5016ed1c796690d857b6525c0d0d484c7676a991bad5925b59",
+                     "bytes_per_launch": 5.408e9}
 
 
 def split_mma_traffic():
