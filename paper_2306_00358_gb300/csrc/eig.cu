@@ -98,10 +98,13 @@ __global__ void __launch_bounds__(256) k_col_normalize(double* Y, int64_t n, int
 constexpr int CHOL_NB = 16;
 __global__ void __launch_bounds__(256) k_chol_flag(const double* G, double* Lout, int m, double tau,
                                                    int* flags, int* nbad) {
-    extern __shared__ double L[];   // m*m row-major, then m of the original diagonal
-    double* gd = L + m * m;
+    // m rows of ld = m + 1 (an odd stride: the rows of one column fall in
+    // different banks), then m of the original diagonal
+    extern __shared__ double L[];
+    const int ld = m + 1;
+    double* gd = L + m * ld;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
-    for (int e = threadIdx.x; e < m * m; e += blockDim.x) L[e] = G[e];
+    for (int e = threadIdx.x; e < m * m; e += blockDim.x) L[(e / m) * ld + e % m] = G[e];
     for (int i = threadIdx.x; i < m; i += blockDim.x) gd[i] = G[(int64_t)i * m + i];
     __syncthreads();
     for (int kb = 0; kb < m; kb += CHOL_NB) {
@@ -110,7 +113,7 @@ __global__ void __launch_bounds__(256) k_chol_flag(const double* G, double* Lout
         if (warp == 0) {
             const int i = kb + lane;
             for (int j = kb; j < kb + nb; ++j) {
-                double d = L[j * m + j];
+                double d = L[j * ld + j];
                 if (lane == 0) {
                     const double gjj = gd[j];
                     if (!(d > tau * gjj) || !isfinite(d)) {
@@ -122,12 +125,12 @@ __global__ void __launch_bounds__(256) k_chol_flag(const double* G, double* Lout
                 d = __shfl_sync(0xffffffffu, d, 0);
                 const double il = rsqrt(d);
                 __syncwarp();
-                if (lane == 0) L[j * m + j] = d * il;
-                if (i > j && lane < nb) L[i * m + j] *= il;
+                if (lane == 0) L[j * ld + j] = d * il;
+                if (i > j && lane < nb) L[i * ld + j] *= il;
                 __syncwarp();
                 if (i > j && lane < nb) {
-                    const double lij = L[i * m + j];
-                    for (int k = j + 1; k <= i; ++k) L[i * m + k] = fma(-lij, L[k * m + j], L[i * m + k]);
+                    const double lij = L[i * ld + j];
+                    for (int k = j + 1; k <= i; ++k) L[i * ld + k] = fma(-lij, L[k * ld + j], L[i * ld + k]);
                 }
                 __syncwarp();
             }
@@ -136,24 +139,25 @@ __global__ void __launch_bounds__(256) k_chol_flag(const double* G, double* Lout
         // 2. panel below it: row i solves x L_kk^T = a (forward substitution)
         for (int i = kb + nb + threadIdx.x; i < m; i += blockDim.x) {
             for (int j = kb; j < kb + nb; ++j) {
-                double a = L[i * m + j];
-                for (int k = kb; k < j; ++k) a = fma(-L[i * m + k], L[j * m + k], a);
-                L[i * m + j] = a / L[j * m + j];
+                double a = L[i * ld + j];
+                for (int k = kb; k < j; ++k) a = fma(-L[i * ld + k], L[j * ld + k], a);
+                L[i * ld + j] = a / L[j * ld + j];
             }
         }
         __syncthreads();
         // 3. trailing matrix: A[i][k] -= sum_t L[i][t] L[k][t], kb+nb <= k <= i
         for (int i = kb + nb + warp; i < m; i += nwarps) {
             for (int k = kb + nb + lane; k <= i; k += 32) {
-                double a = L[i * m + k];
+                double a = L[i * ld + k];
 #pragma unroll 4
-                for (int t = kb; t < kb + nb; ++t) a = fma(-L[i * m + t], L[k * m + t], a);
-                L[i * m + k] = a;
+                for (int t = kb; t < kb + nb; ++t) a = fma(-L[i * ld + t], L[k * ld + t], a);
+                L[i * ld + k] = a;
             }
         }
         __syncthreads();
     }
-    for (int e = threadIdx.x; e < m * m; e += blockDim.x) Lout[e] = ((e % m) <= (e / m)) ? L[e] : 0.0;
+    for (int e = threadIdx.x; e < m * m; e += blockDim.x)
+        Lout[e] = ((e % m) <= (e / m)) ? L[(e / m) * ld + e % m] : 0.0;
 }
 
 // Q = Y L^{-T} row by row, in place allowed: 32 rows per block, the rows in
@@ -257,7 +261,7 @@ __device__ __forceinline__ void rr_pair(int r, int i, int mp, int& p, int& q) {
 }
 
 template <typename T>
-__device__ int jacobi_sweeps(T* H, T* W, int m, T tol, int max_sweeps, T* cs, int* rot, int* pq) {
+__device__ int jacobi_sweeps(T* H, int ld, T* W, int m, T tol, int max_sweeps, T* cs, int* rot, int* pq) {
     const int mp = m + (m & 1);            // even player count (dummy index m when odd)
     const int npair = mp / 2;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
@@ -270,7 +274,7 @@ __device__ int jacobi_sweeps(T* H, T* W, int m, T tol, int max_sweeps, T* cs, in
                 rr_pair(r, i, mp, p, q);
                 T c = 1, s = 0;
                 if (q < m) {
-                    const T hpq = H[p * m + q], hpp = H[p * m + p], hqq = H[q * m + q];
+                    const T hpq = H[p * ld + q], hpp = H[p * ld + p], hqq = H[q * ld + q];
                     if (fabs(hpq) > tol * sqrt(fabs(hpp * hqq)) && fabs(hpq) > (T)1e-300) {
                         const T tau = (hqq - hpp) / (2 * hpq);
                         const T t = (tau >= 0) ? 1 / (tau + sqrt(1 + tau * tau)) : -1 / (-tau + sqrt(1 + tau * tau));
@@ -294,9 +298,9 @@ __device__ int jacobi_sweeps(T* H, T* W, int m, T tol, int max_sweeps, T* cs, in
                 T* wp = W + (int64_t)p * m;
                 T* wq = W + (int64_t)q * m;
                 for (int k = lane; k < m; k += 32) {
-                    const T hkp = H[k * m + p], hkq = H[k * m + q];
-                    H[k * m + p] = c * hkp - s * hkq;
-                    H[k * m + q] = s * hkp + c * hkq;
+                    const T hkp = H[k * ld + p], hkq = H[k * ld + q];
+                    H[k * ld + p] = c * hkp - s * hkq;
+                    H[k * ld + q] = s * hkp + c * hkq;
                     const T vp = wp[k], vq = wq[k];
                     wp[k] = c * vp - s * vq;
                     wq[k] = s * vp + c * vq;
@@ -309,8 +313,8 @@ __device__ int jacobi_sweeps(T* H, T* W, int m, T tol, int max_sweeps, T* cs, in
                 if (s == 0) continue;
                 const T c = cs[2 * i];
                 const int p = pq[2 * i], q = pq[2 * i + 1];
-                T* hp = H + p * m;
-                T* hq = H + q * m;
+                T* hp = H + p * ld;
+                T* hq = H + q * ld;
                 for (int k = lane; k < m; k += 32) {
                     const T hpk = hp[k], hqk = hq[k];
                     hp[k] = c * hpk - s * hqk;
@@ -337,18 +341,21 @@ __device__ int jacobi_sweeps(T* H, T* W, int m, T tol, int max_sweeps, T* cs, in
 //  3. FP64 Jacobi sweeps on H' (it starts ~1e-6 off diagonal, so two or three
 //     quadratically convergent sweeps finish it), W <- W J.
 // Output: theta sorted descending, W (column-major, global) in that order.
-// Shared memory: m*m doubles (H) + m*m doubles (two FP32 m*m arrays, later
-// the Gram/Cholesky matrix and the permutation scratch) + small arrays.
+// Shared memory: H (m rows of ld = m + 1 doubles: the odd stride puts the
+// rows of one column in different banks, so the column updates are
+// conflict-free) + m*ld doubles of scratch (H32 with the same stride and W32,
+// later the Gram/Cholesky matrix) + small arrays.
 __global__ void __launch_bounds__(512) k_jacobi(const double* Hg, int m, double tol, int max_sweeps,
                                                 double* theta, double* Wout, double* T1, int* status,
                                                 int* sweeps_out, int fp64_sweeps) {
     extern __shared__ double sm[];
     const int mp = m + (m & 1);
-    double* H = sm;                            // m*m
-    double* R2 = H + m * m;                    // m*m doubles of scratch
-    float* H32 = (float*)R2;                   // m*m floats
-    float* W32 = H32 + m * m;                  // m*m floats
-    double* cs64 = R2 + m * m;                 // mp
+    const int ld = m + 1;
+    double* H = sm;                            // m*ld
+    double* R2 = H + m * ld;                   // m*ld doubles of scratch
+    float* H32 = (float*)R2;                   // m*ld floats
+    float* W32 = H32 + m * ld;                 // m*m floats
+    double* cs64 = R2 + m * ld;                // mp
     float* cs32 = (float*)(cs64 + mp);         // mp
     int* rot = (int*)(cs32 + mp + (mp & 1));   // 1
     int* perm = rot + 2;                       // m
@@ -360,7 +367,7 @@ __global__ void __launch_bounds__(512) k_jacobi(const double* Hg, int m, double 
     for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
         const int i = e / m, j = e % m;
         const double v = 0.5 * (Hg[(int64_t)i * m + j] + Hg[(int64_t)j * m + i]);
-        H[e] = v;
+        H[i * ld + j] = v;
         lmax = fmax(lmax, fabs(v));
     }
     for (int o = 16; o > 0; o >>= 1) lmax = fmax(lmax, __shfl_xor_sync(0xffffffffu, lmax, o));
@@ -368,12 +375,13 @@ __global__ void __launch_bounds__(512) k_jacobi(const double* Hg, int m, double 
     __syncthreads();
     const double hscale = hmax_s > 0.0 ? 1.0 / hmax_s : 1.0;
     for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
-        H32[e] = (float)(H[e] * hscale);
-        W32[e] = (e / m == e % m) ? 1.0f : 0.0f;
+        const int i = e / m, j = e % m;
+        H32[i * ld + j] = (float)(H[i * ld + j] * hscale);
+        W32[e] = (i == j) ? 1.0f : 0.0f;
     }
     __syncthreads();
     // 1. FP32 sweeps
-    const int s32 = jacobi_sweeps<float>(H32, W32, m, 1e-6f, 40, cs32, rot, pq);
+    const int s32 = jacobi_sweeps<float>(H32, ld, W32, m, 1e-6f, 40, cs32, rot, pq);
     // 2. W (FP64) = W32, then Cholesky-QR of its columns
     for (int e = threadIdx.x; e < m * m; e += blockDim.x) Wout[e] = (double)W32[e];
     __syncthreads();
@@ -412,7 +420,7 @@ __global__ void __launch_bounds__(512) k_jacobi(const double* Hg, int m, double 
     for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
         const int r = e / m, j = e % m;
         double a = 0.0;
-        for (int k = 0; k < m; ++k) a = fma(H[r * m + k], Wout[(int64_t)j * m + k], a);
+        for (int k = 0; k < m; ++k) a = fma(H[r * ld + k], Wout[(int64_t)j * m + k], a);
         T1[(int64_t)r * m + j] = a;
     }
     __syncthreads();
@@ -425,12 +433,16 @@ __global__ void __launch_bounds__(512) k_jacobi(const double* Hg, int m, double 
     __syncthreads();
     for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
         const int i = e / m, j = e % m;
-        H[e] = 0.5 * (G[i * m + j] + G[j * m + i]);
+        H[i * ld + j] = 0.5 * (G[i * m + j] + G[j * m + i]);
     }
     __syncthreads();
     // 3. FP64 sweeps (skipped for a rough Rayleigh-Ritz far from convergence:
-    //    then theta is the diagonal of H' and W the re-orthonormalised W32)
-    const int s64 = fp64_sweeps ? jacobi_sweeps<double>(H, Wout, m, tol, max_sweeps, cs64, rot, pq) : 0;
+    //    then theta is the diagonal of H' and W the re-orthonormalised W32).
+    //    W is accumulated in shared memory (the scratch is free by now).
+    double* Ws = R2;
+    for (int e = threadIdx.x; e < m * m; e += blockDim.x) Ws[e] = Wout[e];
+    __syncthreads();
+    const int s64 = fp64_sweeps ? jacobi_sweeps<double>(H, ld, Ws, m, tol, max_sweeps, cs64, rot, pq) : 0;
     if (threadIdx.x == 0) {
         if (s64 > max_sweeps) atomicOr(status, ST_EIG_NOCONV);
         if (sweeps_out) { atomicAdd(sweeps_out, s32); atomicAdd(sweeps_out + 1, s64); }
@@ -438,18 +450,16 @@ __global__ void __launch_bounds__(512) k_jacobi(const double* Hg, int m, double 
         for (int i = 0; i < m; ++i) {
             int best = i;
             for (int j = i + 1; j < m; ++j)
-                if (H[perm[j] * m + perm[j]] > H[perm[best] * m + perm[best]]) best = j;
+                if (H[perm[j] * ld + perm[j]] > H[perm[best] * ld + perm[best]]) best = j;
             const int x = perm[i]; perm[i] = perm[best]; perm[best] = x;
         }
-        for (int i = 0; i < m; ++i) theta[i] = H[perm[i] * m + perm[i]];
+        for (int i = 0; i < m; ++i) theta[i] = H[perm[i] * ld + perm[i]];
     }
     __syncthreads();
     for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
         const int col = e / m, row = e % m;
-        G[e] = Wout[(int64_t)perm[col] * m + row];
+        Wout[e] = Ws[perm[col] * m + row];
     }
-    __syncthreads();
-    for (int e = threadIdx.x; e < m * m; e += blockDim.x) Wout[e] = G[e];
 }
 
 // max_i<dn |Z_i - theta_i QW_i| / theta_0, as bits of a non-negative double.
@@ -483,7 +493,11 @@ __global__ void k_to_isometry(const double* QW, int64_t n, int dn, double* U) {
 
 static size_t jacobi_smem(int m) {
     const int mp = m + (m & 1);
-    return (size_t)2 * m * m * 8 + (size_t)mp * 8 + (size_t)(mp + 2) * 4 + (size_t)(m + 4) * 4 + (size_t)mp * 4 + 64;
+    return (size_t)2 * m * (m + 1) * 8 + (size_t)mp * 8 + (size_t)(mp + 2) * 4 + (size_t)(m + 4) * 4 + (size_t)mp * 4 + 64;
+}
+
+static size_t chol_smem(int m) {
+    return (size_t)m * (m + 1) * 8 + (size_t)m * 8;
 }
 
 static size_t trsm_smem(int m) {
@@ -524,7 +538,6 @@ static void times_small(Ctx& ctx, const double* A, const double* W, int64_t n, i
 // Orthonormalise the columns of Y in place (two Cholesky-QR passes).
 static void orthonormalise(Ctx& ctx, double* Y, int64_t n, int m, double* G, double* L, int* flags,
                            int* nbad, uint64_t seed, uint64_t& salt) {
-    const size_t smem = (size_t)m * m * sizeof(double);
     for (int pass = 0; pass < 2; ++pass) {
         int attempt = 0;
         for (;; ++attempt) {
@@ -532,7 +545,7 @@ static void orthonormalise(Ctx& ctx, double* Y, int64_t n, int m, double* G, dou
             k_col_normalize<<<m, 256, 0, ctx.stream>>>(Y, n, flags);
             TRG_LAUNCHED(ctx);
             gram(ctx, Y, Y, n, m, G, TRG_FP64);
-            k_chol_flag<<<1, 256, smem + (size_t)m * 8, ctx.stream>>>(G, L, m, pass == 0 ? 1e-8 : 1e-12, flags,
+            k_chol_flag<<<1, 256, chol_smem(m), ctx.stream>>>(G, L, m, pass == 0 ? 1e-8 : 1e-12, flags,
                                                                      nbad);
             TRG_LAUNCHED(ctx);
             int hb = 0;
@@ -558,7 +571,7 @@ int isometry(Ctx& ctx, const double* M, int64_t n, int dcut, double* U, std::vec
     if (m > MAX_M) fail(TRG_ENOTSUP, "isometry: Dcut + oversampling exceeds the supported block (112)");
     static std::once_flag once;
     std::call_once(once, [] {
-        set_smem((const void*)k_chol_flag, (size_t)MAX_M * MAX_M * 8 + MAX_M * 8);
+        set_smem((const void*)k_chol_flag, chol_smem(MAX_M));
         set_smem((const void*)k_trsm_rows, trsm_smem(MAX_M));
         set_smem((const void*)k_jacobi, jacobi_smem(MAX_M));
     });
@@ -688,12 +701,15 @@ int isometry(Ctx& ctx, const double* M, int64_t n, int dcut, double* U, std::vec
         if (!(th[0] > 0.0) || !std::isfinite(th[0])) fail(TRG_ENUMERIC, "environment has no positive eigenvalue");
         if ((res <= tol && full) || m == n) {
             {
-                // products beyond what the tolerance needed (at the rate
-                // theta_m / theta_dn) are dropped from the next plan, one kept spare
+                // The next plan is this solve's product count, one lower when
+                // at least two products were beyond what the tolerance needed
+                // (at the rate theta_m / theta_dn).  Dropping at most one per
+                // solve settles one product above the need: a plan that falls
+                // short costs a second Rayleigh-Ritz, several times a product.
                 const double r = std::min(std::max(th[(size_t)m - 1] / th[(size_t)dn_paper - 1], 0.05), 0.98);
                 const int slack = (res > 0.0 && res < tol) ? (int)std::floor(std::log(tol / res) / -std::log(r)) : 0;
                 hint.n = n; hint.m = m; hint.precision = precision;
-                hint.products = std::max(1, applied - std::max(0, slack - 1));
+                hint.products = std::max(1, applied - (slack >= 2 ? 1 : 0));
             }
             int dn = dn_paper;
             if (ctx.cfg.trunc == TRG_TRUNC_MULTIPLET && dn < n) {
