@@ -701,15 +701,14 @@ int isometry(Ctx& ctx, const double* M, int64_t n, int dcut, double* U, std::vec
         if (!(th[0] > 0.0) || !std::isfinite(th[0])) fail(TRG_ENUMERIC, "environment has no positive eigenvalue");
         if ((res <= tol && full) || m == n) {
             {
-                // The next plan is this solve's product count, one lower when
-                // at least two products were beyond what the tolerance needed
-                // (at the rate theta_m / theta_dn).  Dropping at most one per
-                // solve settles one product above the need: a plan that falls
-                // short costs a second Rayleigh-Ritz, several times a product.
+                // The next plan is this solve's product count less the
+                // products beyond what the tolerance needed (at the rate
+                // theta_m / theta_dn), two kept spare: a plan that falls short
+                // costs a second Rayleigh-Ritz, several times a product.
                 const double r = std::min(std::max(th[(size_t)m - 1] / th[(size_t)dn_paper - 1], 0.05), 0.98);
                 const int slack = (res > 0.0 && res < tol) ? (int)std::floor(std::log(tol / res) / -std::log(r)) : 0;
                 hint.n = n; hint.m = m; hint.precision = precision;
-                hint.products = std::max(1, applied - (slack >= 2 ? 1 : 0));
+                hint.products = std::max(1, applied - std::max(0, slack - 2));
             }
             int dn = dn_paper;
             if (ctx.cfg.trunc == TRG_TRUNC_MULTIPLET && dn < n) {
