@@ -88,71 +88,48 @@ __global__ void __launch_bounds__(256) k_col_normalize(double* Y, int64_t n, int
     for (int64_t r = threadIdx.x; r < n; r += 256) y[r] *= scale;
 }
 
-// Blocked right-looking Cholesky G = L L^T of an m x m Gram matrix of unit
-// columns, in 16-column blocks: warp 0 factors the diagonal block (a lane
-// per row, warp-synchronous), a thread per row solves the panel below it,
-// and a warp per row updates the trailing matrix; three block barriers per
-// block instead of two per column.  A pivot d_j <= tau * G_jj marks column j
-// as dependent (flags[j] = 1, *nbad += 1); the pivot is then replaced by
-// G_jj so the factorisation can continue.
-constexpr int CHOL_NB = 16;
+// Right-looking Cholesky G = L L^T of an m x m Gram matrix of unit columns.
+// Per column: warp 0 takes the pivot and scales the column (also into a
+// broadcast copy), then every warp updates trailing rows, a lane per column.
+// A pivot d_j <= tau * G_jj marks column j as dependent (flags[j] = 1,
+// *nbad += 1); the pivot is then replaced by G_jj so the factorisation can
+// continue.
 __global__ void __launch_bounds__(256) k_chol_flag(const double* G, double* Lout, int m, double tau,
                                                    int* flags, int* nbad) {
     // m rows of ld = m + 1 (an odd stride: the rows of one column fall in
-    // different banks), then m of the original diagonal
+    // different banks), m of the original diagonal, m of column j
     extern __shared__ double L[];
     const int ld = m + 1;
     double* gd = L + m * ld;
+    double* colj = gd + m;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
     for (int e = threadIdx.x; e < m * m; e += blockDim.x) L[(e / m) * ld + e % m] = G[e];
     for (int i = threadIdx.x; i < m; i += blockDim.x) gd[i] = G[(int64_t)i * m + i];
     __syncthreads();
-    for (int kb = 0; kb < m; kb += CHOL_NB) {
-        const int nb = min(CHOL_NB, m - kb);
-        // 1. diagonal block, warp 0: lane i owns row kb + i
+    for (int j = 0; j < m; ++j) {
         if (warp == 0) {
-            const int i = kb + lane;
-            for (int j = kb; j < kb + nb; ++j) {
-                double d = L[j * ld + j];
-                if (lane == 0) {
-                    const double gjj = gd[j];
-                    if (!(d > tau * gjj) || !isfinite(d)) {
-                        flags[j] = 1;
-                        atomicAdd(nbad, 1);
-                        d = (gjj > 0.0 && isfinite(gjj)) ? gjj : 1.0;
-                    }
+            double d = L[j * ld + j];
+            if (lane == 0) {
+                const double gjj = gd[j];
+                if (!(d > tau * gjj) || !isfinite(d)) {
+                    flags[j] = 1;
+                    atomicAdd(nbad, 1);
+                    d = (gjj > 0.0 && isfinite(gjj)) ? gjj : 1.0;
                 }
-                d = __shfl_sync(0xffffffffu, d, 0);
-                const double il = rsqrt(d);
-                __syncwarp();
-                if (lane == 0) L[j * ld + j] = d * il;
-                if (i > j && lane < nb) L[i * ld + j] *= il;
-                __syncwarp();
-                if (i > j && lane < nb) {
-                    const double lij = L[i * ld + j];
-                    for (int k = j + 1; k <= i; ++k) L[i * ld + k] = fma(-lij, L[k * ld + j], L[i * ld + k]);
-                }
-                __syncwarp();
+            }
+            d = __shfl_sync(0xffffffffu, d, 0);
+            const double il = rsqrt(d);
+            if (lane == 0) L[j * ld + j] = d * il;
+            for (int i = j + 1 + lane; i < m; i += 32) {
+                const double v = L[i * ld + j] * il;
+                L[i * ld + j] = v;
+                colj[i] = v;
             }
         }
         __syncthreads();
-        // 2. panel below it: row i solves x L_kk^T = a (forward substitution)
-        for (int i = kb + nb + threadIdx.x; i < m; i += blockDim.x) {
-            for (int j = kb; j < kb + nb; ++j) {
-                double a = L[i * ld + j];
-                for (int k = kb; k < j; ++k) a = fma(-L[i * ld + k], L[j * ld + k], a);
-                L[i * ld + j] = a / L[j * ld + j];
-            }
-        }
-        __syncthreads();
-        // 3. trailing matrix: A[i][k] -= sum_t L[i][t] L[k][t], kb+nb <= k <= i
-        for (int i = kb + nb + warp; i < m; i += nwarps) {
-            for (int k = kb + nb + lane; k <= i; k += 32) {
-                double a = L[i * ld + k];
-#pragma unroll 4
-                for (int t = kb; t < kb + nb; ++t) a = fma(-L[i * ld + t], L[k * ld + t], a);
-                L[i * ld + k] = a;
-            }
+        for (int i = j + 1 + warp; i < m; i += nwarps) {
+            const double li = colj[i];
+            for (int k = j + 1 + lane; k <= i; k += 32) L[i * ld + k] = fma(-li, colj[k], L[i * ld + k]);
         }
         __syncthreads();
     }
@@ -160,18 +137,18 @@ __global__ void __launch_bounds__(256) k_chol_flag(const double* G, double* Lout
         Lout[e] = ((e % m) <= (e / m)) ? L[(e / m) * ld + e % m] : 0.0;
 }
 
-// Q = Y L^{-T} row by row, in place allowed: 32 rows per block, the rows in
-// shared memory.  Blocked by 16 columns: warp 0 solves the diagonal block (a
-// lane per row, a short dependent chain), then all four warps subtract the
-// block from the columns to its right (independent FMAs, so the SM's FP64
-// pipes stay busy); two block barriers per 16 columns.
+// Q = Y L^{-T} row by row, in place allowed: 32 rows per block, a lane per
+// row, the solution in shared memory.  Right-looking: after x_j is known,
+// every later column k subtracts L[k][j] x_j.  Column k belongs to warp
+// k % 4, so the four warps (and the SM's four FP64 pipes) share the updates
+// and x_j needs no reduction, one block barrier per column.
 constexpr int TRSM_ROWS = 32;
 constexpr int TRSM_THREADS = 128;
-constexpr int TRSM_NB = 16;
 __global__ void __launch_bounds__(TRSM_THREADS) k_trsm_rows(double* Y, const double* Lg, int64_t n, int m) {
-    extern __shared__ double L[];   // m*m, m inverse diagonals, TRSM_ROWS rows of m + 1
+    extern __shared__ double L[];   // m*m, m inverse diagonals, TRSM_ROWS rows of m + 1, 2 x TRSM_ROWS x_j
     double* dinv = L + m * m;
     double* rows = dinv + m;
+    double* xb = rows + TRSM_ROWS * (m + 1);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     for (int e = threadIdx.x; e < m * m; e += blockDim.x) L[e] = Lg[e];
     for (int i = threadIdx.x; i < m; i += blockDim.x) dinv[i] = 1.0 / Lg[(int64_t)i * m + i];
@@ -181,27 +158,20 @@ __global__ void __launch_bounds__(TRSM_THREADS) k_trsm_rows(double* Y, const dou
         rows[t * (m + 1) + j] = (r0 + t < n) ? Y[(int64_t)j * n + r0 + t] : 0.0;
     }
     __syncthreads();
-    for (int kb = 0; kb < m; kb += TRSM_NB) {
-        const int nb = min(TRSM_NB, m - kb);
-        if (warp == 0) {
-            double* y = rows + lane * (m + 1);
-            for (int j = kb; j < kb + nb; ++j) {
-                double a = y[j];
-                for (int k = kb; k < j; ++k) a = fma(-L[j * m + k], y[k], a);
-                y[j] = a * dinv[j];
-            }
+    double* y = rows + lane * (m + 1);
+    for (int j = 0; j < m; ++j) {
+        double* xs = xb + (j & 1) * TRSM_ROWS;
+        if (warp == (j & 3)) {
+            const double x = y[j] * dinv[j];
+            y[j] = x;
+            xs[lane] = x;
         }
         __syncthreads();
-        // columns j >= kb + nb: thread (row = lane, every 4th column from warp)
-        double* y = rows + lane * (m + 1);
-        for (int j = kb + nb + warp; j < m; j += 4) {
-            double a = y[j];
-#pragma unroll 4
-            for (int t = kb; t < kb + nb; ++t) a = fma(-L[j * m + t], y[t], a);
-            y[j] = a;
-        }
-        __syncthreads();
+        const double x = xs[lane];
+        int k = j + 1 + ((warp - (j + 1)) & 3);      // first column > j owned by this warp
+        for (; k < m; k += 4) y[k] = fma(-L[k * m + j], x, y[k]);
     }
+    __syncthreads();
     for (int e = threadIdx.x; e < m * TRSM_ROWS; e += blockDim.x) {
         const int j = e / TRSM_ROWS, t = e % TRSM_ROWS;
         if (r0 + t < n) Y[(int64_t)j * n + r0 + t] = rows[t * (m + 1) + j];
@@ -497,11 +467,11 @@ static size_t jacobi_smem(int m) {
 }
 
 static size_t chol_smem(int m) {
-    return (size_t)m * (m + 1) * 8 + (size_t)m * 8;
+    return (size_t)m * (m + 1) * 8 + (size_t)m * 16;
 }
 
 static size_t trsm_smem(int m) {
-    return (size_t)m * m * 8 + (size_t)m * 8 + (size_t)TRSM_ROWS * (m + 1) * 8;
+    return (size_t)m * m * 8 + (size_t)m * 8 + (size_t)TRSM_ROWS * (m + 1) * 8 + 2 * TRSM_ROWS * 8;
 }
 
 static void set_smem(const void* fn, size_t bytes) {
