@@ -767,35 +767,41 @@ k_split_mma(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
                     const int nt = nb * BN + colh * CPT;
                     if constexpr (MODE == EPI_DIRECT) {
                         // rows adjacent in C: form, record and store each result in one
-                        // pass (the lanes, adjacent rows, write 256 contiguous bytes)
-                        if (row_ok) {
-                            double* cp = g.C + g.c_m[m] + g.c_n[nt];
-                            const int64_t step = g.c_col_stride;
-                            const int64_t cm0 = g.cons_ef ? g.cons_m[m] : 0;
-                            int64_t cur = -1;
-                            int cur_max = 0;
+                        // pass (the lanes, adjacent rows, write 256 contiguous bytes).
+                        // The warp's 32 columns are the same for every lane: lane j
+                        // loads column j's exponent and consumer-row offset once and
+                        // the loop takes them by shuffle, so no global load waits
+                        // inside it.
+                        const bool col_in = nt + lane < g.N;
+                        const int eb_l = col_in ? g.eb[nt + lane] - 36 : 0;
+                        const long long cn_l = (g.cons_ef && col_in) ? (long long)g.cons_n[nt + lane] : 0;
+                        double* cp = g.C + (row_ok ? g.c_m[m] + g.c_n[nt] : 0);
+                        const int64_t step = g.c_col_stride;
+                        const int64_t cm0 = (g.cons_ef && row_ok) ? g.cons_m[m] : 0;
+                        int64_t cur = -1;
+                        int cur_max = 0;
 #pragma unroll
-                            for (int j = 0; j < CPT; ++j) {
-                                const int n = nt + j;
-                                if (n < g.N) {
-                                    const double v = scaled_i64_to_double(J[j], ea + g.eb[n] - 36);
-                                    *cp = v;
-                                    if (g.cons_ef) {
-                                        const int64_t crow = cm0 + g.cons_n[n];
-                                        const int ef = (int)(((unsigned long long)__double_as_longlong(v) >> 52) & 0x7FF);
-                                        if (crow != cur) {
-                                            if (cur >= 0 && cur_max) atomicMax(&g.cons_ef[cur], cur_max);
-                                            cur = crow;
-                                            cur_max = ef;
-                                        } else {
-                                            cur_max = max(cur_max, ef);
-                                        }
+                        for (int j = 0; j < CPT; ++j) {
+                            const int e2 = ea + __shfl_sync(0xffffffffu, eb_l, j);
+                            const long long cn = __shfl_sync(0xffffffffu, cn_l, j);
+                            if (row_ok && nt + j < g.N) {
+                                const double v = scaled_i64_to_double(J[j], e2);
+                                *cp = v;
+                                if (g.cons_ef) {
+                                    const int64_t crow = cm0 + cn;
+                                    const int ef = (int)(((unsigned long long)__double_as_longlong(v) >> 52) & 0x7FF);
+                                    if (crow != cur) {
+                                        if (cur >= 0 && cur_max) atomicMax(&g.cons_ef[cur], cur_max);
+                                        cur = crow;
+                                        cur_max = ef;
+                                    } else {
+                                        cur_max = max(cur_max, ef);
                                     }
                                 }
-                                cp += step;
                             }
-                            if (cur >= 0 && cur_max) atomicMax(&g.cons_ef[cur], cur_max);
+                            cp += step;
                         }
+                        if (cur >= 0 && cur_max) atomicMax(&g.cons_ef[cur], cur_max);
                         continue;
                     }
                     if constexpr (MODE == EPI_STAGED) {
