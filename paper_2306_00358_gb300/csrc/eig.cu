@@ -650,7 +650,11 @@ int isometry(Ctx& ctx, const double* M, int64_t n, int dcut, double* U, std::vec
         gram(ctx, Q, Y, n, m, G, TRG_FP64);
         TRG_CUDA(cudaMemsetAsync(sweeps, 0, 2 * sizeof(int), ctx.stream));
         const int full = (rr_done > 0 || m == n) ? 1 : 0;
-        k_jacobi<<<1, 512, jac_smem, ctx.stream>>>(G, m, 1e-15, 60, theta, W, L, status, sweeps, full);
+        // FP64 rotations stop at |h_pq| <= 1e-13 sqrt(h_pp h_qq): the FP32 sweeps
+        // leave ~1e-7, one quadratically convergent FP64 sweep ~1e-14, so the
+        // next sweep only confirms (the eigenvalues are then exact to ~1e-26
+        // relative, the vectors of pairs with a relative gap g to ~1e-13 / g)
+        k_jacobi<<<1, 512, jac_smem, ctx.stream>>>(G, m, 1e-13, 60, theta, W, L, status, sweeps, full);
         TRG_LAUNCHED(ctx);
         times_small(ctx, Y, W, n, m, Z);
         times_small(ctx, Q, W, n, m, QW);
