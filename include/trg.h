@@ -72,7 +72,7 @@ typedef struct trg_config {
     int trunc;               /* trg_trunc (default TRG_TRUNC_PAPER) */
     double gap_tol;          /* multiplet gap, relative to lambda_1 (default 1e-6; in
                                 TRG_SPLIT_BF16 at least 2^-(8*split_slices-12)) */
-    int oversample;          /* subspace-iteration oversampling p (default 16) */
+    int oversample;          /* subspace-iteration oversampling p (default 24; at most 112 - Dcut) */
     double eig_tol;          /* Ritz residual tolerance relative to lambda_1 (default 1e-12; in
                                 TRG_SPLIT_BF16 at least 2^-(8*split_slices-10)) */
     int eig_max_iter;        /* subspace iterations before TRG_ENUMERIC (default 300) */

@@ -249,7 +249,7 @@ int trg_config_default(trg_config* cfg) {
     cfg->split_from_step = 0;
     cfg->trunc = TRG_TRUNC_PAPER;
     cfg->gap_tol = 1e-6;
-    cfg->oversample = 16;
+    cfg->oversample = 24;
     cfg->eig_tol = 1e-12;
     cfg->eig_max_iter = 300;
     cfg->seed = 0x5EEDull;

@@ -537,8 +537,11 @@ static void orthonormalise(Ctx& ctx, double* Y, int64_t n, int m, double* G, dou
 int isometry(Ctx& ctx, const double* M, int64_t n, int dcut, double* U, std::vector<double>& lam,
              int step, int precision) {
     const int dn_paper = (int)std::min<int64_t>(n, dcut);
-    const int m = (int)std::min<int64_t>(n, (int64_t)dn_paper + std::max(1, ctx.cfg.oversample));
-    if (m > MAX_M) fail(TRG_ENOTSUP, "isometry: Dcut + oversampling exceeds the supported block (112)");
+    // block of dn + p columns, at most the shared-memory block of the small
+    // kernels (p shrinks there: Dcut 96 runs with p = 16)
+    if (dn_paper >= MAX_M && dn_paper < n)
+        fail(TRG_ENOTSUP, "isometry: Dcut above the supported block (111 kept vectors)");
+    const int m = (int)std::min<int64_t>({n, (int64_t)dn_paper + std::max(1, ctx.cfg.oversample), (int64_t)MAX_M});
     static std::once_flag once;
     std::call_once(once, [] {
         set_smem((const void*)k_chol_flag, chol_smem(MAX_M));

@@ -38,7 +38,7 @@ size_t estimate_bytes(const trg_solve_spec& s, size_t workspace_cap) {
     const double d0 = (s.model == TRG_ISING) ? 2 : std::max(1, s.D0);
     const double D = std::max<double>(d0, std::min<double>(s.Dcut, std::max(d0 * d0, (double)s.Dcut)));
     const double D2 = D * D, D4 = D2 * D2;
-    const double m = std::min<double>(D2, s.Dcut + 16);
+    const double m = std::min<double>({D2, s.Dcut + 24.0, 112.0});
     double bytes = 0;
     bytes += 2 * D4 * 8;                       // T, Tnext
     bytes += 3 * D4 * 8;                       // M, P, Q

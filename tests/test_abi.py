@@ -50,7 +50,7 @@ def test_status_strings_and_defaults():
     assert lib.trg_config_default(ctypes.byref(cfg)) == 0
     assert cfg.precision == _lib.TRG_FP64
     assert cfg.split_slices == 4
-    assert cfg.oversample == 16
+    assert cfg.oversample == 24
     assert cfg.eig_tol == 1e-12
     assert lib.trg_config_default(None) == _lib.TRG_EINVAL
 
