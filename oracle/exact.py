@@ -19,6 +19,9 @@ ORACLE / TEST INFRASTRUCTURE ONLY.
       ln Z / V = (1/2) ln q + 2 int_0^inf sinh((pi - mu) x) tanh(mu x) / (x sinh(pi x)) dx,
       sqrt(q) = 2 cos(mu).
   It reduces to 2 ln 2 at q = 1 and to Onsager's value plus K_c at q = 2.
+* Brute-force partition function of the Ising model on small periodic
+  cubic lattices (every site bonds to its +x, +y and +z neighbours, a
+  lattice one site wide bonding a site to itself), for the 3D blocking.
 * Brute-force partition functions of small periodic lattices: Ising by
   enumerating spins, XY by enumerating bond charges of the character
   expansion.  Bonds: every site couples to its right and its upper
@@ -181,6 +184,22 @@ def onsager_yang_magnetization(beta: float) -> float:
     if beta <= BETA_C:
         return 0.0
     return (1.0 - math.sinh(2.0 * beta) ** -4) ** 0.125
+
+
+def ising3d_lnz_exact(lx: int, ly: int, lz: int, beta: float, h: float = 0.0) -> float:
+    """ln Z of the Ising model on an lx x ly x lz torus by enumeration:
+    Z = sum_s exp(beta sum_<ij> s_i s_j + beta h sum_i s_i) over the 3 V bonds
+    (i, i + e) for e = x, y, z (periodic)."""
+    nsite = lx * ly * lz
+    if nsite > 20:
+        raise ValueError("lattice too large to enumerate")
+    states = np.arange(2 ** nsite, dtype=np.int64)
+    s = (1 - 2 * ((states[:, None] >> np.arange(nsite)) & 1)).reshape(-1, lz, ly, lx)
+    bond = (np.sum(s * np.roll(s, -1, axis=3), axis=(1, 2, 3)) + np.sum(s * np.roll(s, -1, axis=2), axis=(1, 2, 3))
+            + np.sum(s * np.roll(s, -1, axis=1), axis=(1, 2, 3)))
+    e = beta * bond + beta * h * np.sum(s, axis=(1, 2, 3))
+    emax = float(np.max(e))
+    return emax + math.log(float(np.sum(np.exp(e - emax))))
 
 
 def potts_critical_lnz(q: float) -> float:
