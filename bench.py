@@ -66,6 +66,10 @@ def parse():
     ap.add_argument("--fields-m", default="1e-5,3e-5,1e-4,3e-4,1e-3")
     ap.add_argument("--dcut-m", type=int, default=64)
     ap.add_argument("--steps-m", type=int, default=72, help="half-steps: 72 = a 2^36 x 2^36 lattice")
+    ap.add_argument("--hotrg3d", action="store_true",
+                    help="cubic-lattice Ising solves (the 3D blocking): seconds per step, split vs FP64")
+    ap.add_argument("--dcuts-3d", default="8,12")
+    ap.add_argument("--steps-3d", type=int, default=12)
     ap.add_argument("--serve", action="store_true", help="config 5: Poisson stream of requests")
     ap.add_argument("--requests", type=int, default=200)
     ap.add_argument("--rate", type=float, default=2.0, help="serve: mean arrivals per second")
@@ -619,6 +623,50 @@ def run_potts(args):
     print(json.dumps(line), flush=True)
 
 
+def run_hotrg3d(args):
+    """Cubic-lattice Ising at beta_c = 0.2216544 (the 3D blocking, the
+    paper's future-work direction): one whole solve per Dcut and precision,
+    timed with CUDA events; seconds per step, the split products' rate, and
+    |ln Z/V (split) - ln Z/V (FP64)|."""
+    import torch
+
+    from paper_2306_00358_gb300 import Solver
+
+    beta = 0.2216544
+    out = []
+    for dcut in [int(d) for d in args.dcuts_3d.split(",")]:
+        row = {"dcut": dcut, "steps": args.steps_3d, "lattice": "2^%d sites" % args.steps_3d}
+        for precision in ("split", "fp64"):
+            if precision == "fp64" and dcut > 12:
+                continue      # the FP64 pipe: ~30 s per step at Dcut 16
+            stream = torch.cuda.current_stream()
+            # multiplet truncation: the cubic symmetry makes exactly degenerate
+            # eigenvalues at some cuts (Dcut 8, step 2), which split and FP64
+            # runs would otherwise cut differently
+            with Solver(0, stream=stream, precision=precision, trunc="multiplet") as s:
+                s.solve3d(beta, 0.0, dcut, min(3, args.steps_3d))    # warm-up (tables, buffers)
+                s.profile(True)
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                torch.cuda.synchronize()
+                e0.record(stream)
+                f, lnz = s.solve3d(beta, 0.0, dcut, args.steps_3d)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                ph = s.phase_stats()
+                s.profile(False)
+            sec = e0.elapsed_time(e1) / 1e3
+            row[precision] = {"f": f, "lnz_per_site": lnz, "seconds": sec, "s_per_step": sec / args.steps_3d,
+                              "phases_ms": {k: round(v["ms"], 3) for k, v in ph.items()}}
+            if precision == "split" and ph["mma"]["ms"] > 0:
+                row[precision]["mma_tflops"] = ph["mma"]["mma_flops"] / (ph["mma"]["ms"] / 1e3) / 1e12
+        if "fp64" in row:
+            row["abs_dlnz_split_fp64"] = abs(row["split"]["lnz_per_site"] - row["fp64"]["lnz_per_site"])
+        print(json.dumps(row), flush=True)
+        out.append(row)
+    print(json.dumps({"mode": "hotrg3d", "model": "ising", "beta": beta, "runs": len(out)}), flush=True)
+
+
 def run_magnetization(args):
     """Magnetization of the XY model at T_c = 0.89290 versus the field h, from
     an impure tensor with cos(theta) inserted (the study of Sec. 3.1: exponent
@@ -663,6 +711,9 @@ def main():
     args = parse()
     if args.magnetization:
         run_magnetization(args)
+        return
+    if args.hotrg3d:
+        run_hotrg3d(args)
         return
     if args.potts:
         run_potts(args)

@@ -177,6 +177,34 @@ int trg_coarse_grain(trg_ctx* ctx, int Dcut, int nsteps);
  */
 int trg_free_energy(trg_ctx* ctx, double* f_out, double* lnz_per_site);
 
+/* ------------------------------------------------------- cubic lattice */
+/*
+ * A whole solve of the Ising model on the cubic lattice, the direction the
+ * paper leaves to future work (Sec. 1, Sec. 4), blocked as the 2D variant of
+ * Sec. 2 with a third pair of legs.  The site tensor is
+ *   T[x,x',y,y',z,z'] = sum_s e^{beta h s} W[s,x] W[s,x'] W[s,y] W[s,y'] W[s,z] W[s,z'],
+ * W the symmetric square root of the bond matrix (D0 = 2).  Each step stacks
+ * two tensors along z; the left/right leg pairs are truncated to
+ * Nx = min(Dx^2, Dcut) by one isometry from the environment of the two left
+ * legs (Gram matrix of the stacked pair over its other legs), the
+ * front/back pairs likewise by one from the two front legs; then the axes
+ * rotate so that the steps block z, x, y, z, ...  Normalisation by max|T|
+ * after each step; ln Z / V = ln n0 + sum_k 2^-k ln n_k + 2^-N ln Tr T_N,
+ * Tr T = sum T[x,x,y,y,z,z], for the periodic Lx x Ly x Lz lattice with
+ * Lz = 2^ceil(N/3), Lx = 2^ceil((N-1)/3), Ly = 2^floor(N/3).
+ * model: TRG_ISING only (else TRG_ENOTSUP); beta > 0 and finite, h finite,
+ * Dcut >= 1, 0 <= nsteps <= 300 (else TRG_EINVAL).  The precision settings
+ * of the context apply.  Outputs f = -(ln Z / V) / beta and ln Z / V (either
+ * pointer may be NULL, not both).  The kept eigenvalues of step k's two
+ * isometries are available as trg_get_spectrum steps 2k-1 (x) and 2k (y).
+ * The context's 2D state is cleared (trg_coarse_grain then needs a new
+ * trg_init_tensor).  Device memory: about 8 (Dx^2 Dy^4 Dz^2 + 3 Dcut D^6)
+ * bytes for the largest step.  Errors: TRG_ENOMEM, TRG_ENUMERIC (norm or
+ * trace not positive, eigensolver), TRG_ECUDA.
+ */
+int trg_solve3d(trg_ctx* ctx, int model, double beta, double h, int Dcut, int nsteps, double* f_out,
+                double* lnz_per_site);
+
 /* Kept eigenvalues of M at half-step `step` (1-based), descending, written
  * to out[0..min(cap,n)-1]; *n_out = number kept.  Untruncated steps (U = I)
  * report n_out = 0. */

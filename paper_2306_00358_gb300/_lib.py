@@ -91,6 +91,7 @@ SIGNATURES = {
     "trg_expectation": (c_int, [c_void_p, P_double]),
     "trg_coarse_grain": (c_int, [c_void_p, c_int, c_int]),
     "trg_free_energy": (c_int, [c_void_p, P_double, P_double]),
+    "trg_solve3d": (c_int, [c_void_p, c_int, c_double, c_double, c_int, c_int, P_double, P_double]),
     "trg_get_spectrum": (c_int, [c_void_p, c_int, P_double, c_int, P_int]),
     "trg_get_state": (c_int, [c_void_p, P_int, P_int, P_int, P_double]),
     "trg_get_tensor": (c_int, [c_void_p, P_double, c_size_t]),

@@ -315,9 +315,13 @@ int trg_destroy(trg_ctx* ctx) {
                         &c.eig_small, &c.flags, &c.split_ws, &c.f64_partial, &c.cons_ef, &c.Timp, &c.Timp_next,
                         &c.Timp_tmp, &c.eig_slices})
         c.release(*b);
+    for (trg::Buf& b : c.s3) c.release(b);
     for (auto& kv : c.tables) c.release(kv.second);
     c.tables.clear();
-    c.collect_timings();
+    try {
+        c.collect_timings();   // a context whose stream has failed still frees its resources
+    } catch (const trg::Error&) {
+    }
     for (cudaEvent_t e : c.event_pool) cudaEventDestroy(e);
     delete ctx;
     return TRG_OK;
@@ -493,6 +497,65 @@ int trg_free_energy(trg_ctx* ctx, double* f_out, double* lnz_per_site) {
     const double lnz = h[trg::SC_LN_N0] + h[trg::SC_LOGNORM] + std::ldexp(std::log(h[trg::SC_TRACE]), -ctx->steps);
     if (lnz_per_site) *lnz_per_site = lnz;
     if (f_out) *f_out = -lnz / ctx->beta;
+    return TRG_OK;
+    TRG_GUARD_END(ctx)
+}
+
+int trg_solve3d(trg_ctx* ctx, int model, double beta, double h, int Dcut, int nsteps, double* f_out,
+                double* lnz_per_site) {
+    if (!ctx) return TRG_EINVAL;
+    if (model != TRG_ISING) return bad(ctx, TRG_ENOTSUP, "solve3d: the cubic-lattice path has the Ising model only");
+    if (!(beta > 0.0) || !std::isfinite(beta) || !std::isfinite(h))
+        return bad(ctx, TRG_EINVAL, "solve3d: beta > 0 and finite h required");
+    if (Dcut < 1 || nsteps < 0 || nsteps > 300) return bad(ctx, TRG_EINVAL, "solve3d: Dcut >= 1, 0 <= nsteps <= 300");
+    if (!f_out && !lnz_per_site) return bad(ctx, TRG_EINVAL, "no output");
+    TRG_GUARD_BEGIN
+    trg::Ctx& c = *ctx;
+    TRG_CUDA(cudaSetDevice(c.device));
+    reset_solve(c);
+    c.ensure(c.T, 64 * sizeof(double));
+    trg::launch_init_ising3d(c, c.T.as<double>(), beta, h);
+    trg::launch_normalise(c, c.T.as<double>(), 64, 0, true);
+    if (trg::read_status(c) & trg::ST_BAD_NORM) return bad(ctx, TRG_ENUMERIC, "initial tensor has no positive norm");
+    auto contiguous = [](double* p, const int64_t* n) {
+        trg::View6 v;
+        v.p = p;
+        int64_t stride = 1;
+        for (int i = 5; i >= 0; --i) { v.n[i] = n[i]; v.s[i] = stride; stride *= n[i]; }
+        return v;
+    };
+    int64_t dims[6] = {2, 2, 2, 2, 2, 2};
+    trg::View6 v = contiguous(c.T.as<double>(), dims);
+    for (int k = 1; k <= nsteps; ++k) {
+        const int64_t Dx = v.n[0], Dy = v.n[2], Dz = v.n[4];
+        const int64_t Nx = std::min<int64_t>(Dx * Dx, Dcut), Ny = std::min<int64_t>(Dy * Dy, Dcut);
+        c.ensure(c.Tnext, (size_t)(Nx * Nx * Ny * Ny * Dz * Dz) * sizeof(double));
+        std::vector<double> lx, ly;
+        const auto kept = trg::step3(c, v, Dcut, k, c.Tnext.as<double>(), trg::precision_for_step(c, k), lx, ly);
+        const int64_t kx = kept.first, ky = kept.second;
+        c.phase = TRG_PHASE_NORM;
+        trg::launch_normalise(c, c.Tnext.as<double>(), kx * kx * ky * ky * Dz * Dz, k, false);
+        if (trg::read_status(c) & trg::ST_BAD_NORM)
+            return bad(ctx, TRG_ENUMERIC, ("non-positive or non-finite norm at step " + std::to_string(k)).c_str());
+        std::swap(c.T, c.Tnext);
+        // the next axis to block into the z slot: a rotation of the view
+        const int64_t out_dims[6] = {kx, kx, ky, ky, Dz, Dz};
+        const trg::View6 w = contiguous(c.T.as<double>(), out_dims);
+        for (int i = 0; i < 6; ++i) { v.n[i] = w.n[(i + 2) % 6]; v.s[i] = w.s[(i + 2) % 6]; }
+        v.p = w.p;
+        c.spectra.push_back(lx);
+        c.spectra.push_back(ly);
+    }
+    double* scal = c.scal.as<double>();
+    trg::launch_trace3(c, v, scal + trg::SC_TRACE);
+    double hs[trg::SC_COUNT];
+    TRG_CUDA(cudaMemcpyAsync(hs, scal, sizeof(hs), cudaMemcpyDeviceToHost, c.stream));
+    TRG_CUDA(cudaStreamSynchronize(c.stream));
+    if (trg::read_status(c) & trg::ST_BAD_TRACE) return bad(ctx, TRG_ENUMERIC, "non-positive trace");
+    const double lnz = hs[trg::SC_LN_N0] + hs[trg::SC_LOGNORM] + std::ldexp(std::log(hs[trg::SC_TRACE]), -nsteps);
+    if (lnz_per_site) *lnz_per_site = lnz;
+    if (f_out) *f_out = -lnz / beta;
+    c.have_tensor = false;   // the 2D state does not survive a cubic-lattice solve
     return TRG_OK;
     TRG_GUARD_END(ctx)
 }

@@ -219,6 +219,7 @@ void trim_buffers(Ctx& c) {
                    &c.split_ws, &c.f64_partial, &c.cons_ef, &c.eig_slices, &c.Timp,
                    &c.Timp_next, &c.Timp_tmp})
         c.release(*b);
+    for (Buf& b : c.s3) c.release(b);
     for (auto& kv : c.tables) c.release(kv.second);
     c.tables.clear();
     c.have_tensor = false;

@@ -6,6 +6,7 @@
 #include <cstdint>
 #include <map>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "trg.h"
@@ -48,6 +49,13 @@ struct View4 {
     int64_t s[4];
 };
 
+// A rank-6 strided view (the cubic-lattice tensor t[x, x', y, y', z, z']).
+struct View6 {
+    double* p;
+    int64_t n[6];
+    int64_t s[6];
+};
+
 struct Ctx {
     int device = 0;
     int sm_count = 0;
@@ -86,6 +94,7 @@ struct Ctx {
     Buf f64_partial;       // FP64 GEMM: split-K partial sums
     Buf cons_ef;           // exponent fields recorded by a producing product (two halves)
     Buf eig_slices;        // split mode: M sliced once per isometry solve
+    Buf s3[10];            // cubic-lattice step: P1, P2, Mx, My, Ux, Uy and the contraction intermediates
     std::map<std::string, Buf> tables;  // cached offset tables
 
     // ---- phase timing
@@ -220,6 +229,14 @@ void launch_trace(Ctx& ctx, const double* T, int64_t Dx, int64_t Dy, double* slo
 void launch_identity(Ctx& ctx, double* U, int64_t n);
 void launch_fill(Ctx& ctx, double* x, int64_t n, double v);
 void launch_copy_strided(Ctx& ctx, const View4& src, const View4& dst);
+
+// Cubic lattice (path3d.cu, small_kernels.cu)
+void launch_init_ising3d(Ctx& ctx, double* T, double beta, double h);
+void launch_trace3(Ctx& ctx, const View6& t, double* slot);
+// One z step of the view t into out (contiguous [X][X'][Y][Y'][z][z']);
+// returns (Nx, Ny) and appends the kept eigenvalues of both isometries.
+std::pair<int64_t, int64_t> step3(Ctx& ctx, const View6& t, int dcut, int step, double* out, int precision,
+                                  std::vector<double>& lam_x, std::vector<double>& lam_y);
 
 int read_status(Ctx& ctx);  // synchronises the stream
 void trim_buffers(Ctx& ctx);  // free every solve buffer (engine.cu)

@@ -45,6 +45,44 @@ __global__ void k_init_ising(double* T, double beta, double h, int impure) {
     T[e] = t;
 }
 
+// Cubic-lattice Ising: T[x,x',y,y',z,z'] = sum_s e^{beta h s} W[s,x] W[s,x']
+// W[s,y] W[s,y'] W[s,z] W[s,z'] (the 2D construction with two more legs).
+__global__ void k_init_ising3d(double* T, double beta, double h) {
+    const int e = threadIdx.x;
+    if (e >= 64) return;
+    const double a = sqrt(2.0 * cosh(beta));
+    const double b = beta > 0.0 ? sqrt(2.0 * sinh(beta)) : 0.0;
+    const double w[2][2] = {{0.5 * (a + b), 0.5 * (a - b)}, {0.5 * (a - b), 0.5 * (a + b)}};
+    double t = 0.0;
+    for (int s = 0; s < 2; ++s) {
+        const double spin = s == 0 ? 1.0 : -1.0;
+        double p = exp(beta * h * spin);
+        for (int leg = 0; leg < 6; ++leg) p *= w[s][(e >> (5 - leg)) & 1];
+        t += p;
+    }
+    T[e] = t;
+}
+
+// Tr T = sum_{x,y,z} T[x,x,y,y,z,z] of a strided rank-6 view (dims n, strides s)
+__global__ void __launch_bounds__(256) k_trace3(const double* T, int64_t nx, int64_t ny, int64_t nz, int64_t sx,
+                                                int64_t sy, int64_t sz, double* out, int* status) {
+    double acc = 0.0;
+    for (int64_t e = threadIdx.x; e < nx * ny * nz; e += 256) {
+        const int64_t z = e % nz, y = (e / nz) % ny, x = e / nz / ny;
+        acc += T[x * sx + y * sy + z * sz];
+    }
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    __shared__ double red[8];
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < 8; ++w) t += red[w];
+        *out = t;
+        if (!(t > 0.0) || !isfinite(t)) atomicOr(status, ST_BAD_TRACE);
+    }
+}
+
 // XY (character expansion, |n| <= nmax, index = n + nmax):
 // T[nl,nu,nr,nd] = prod sqrt(I_n(beta)) * I_{nl+nu-nr-nd}(beta h)
 // impure: cos(theta) inserted; cos = (e^{i theta} + e^{-i theta}) / 2 turns the
@@ -238,6 +276,17 @@ void launch_normalise(Ctx& ctx, double* x, int64_t n, int k, bool initial) {
     k_scale_by_norm<<<grid_for(ctx, n, 256), 256, 0, ctx.stream>>>(x, n, (const unsigned long long*)(scal + SC_NORM));
     TRG_LAUNCHED(ctx);
     k_lognorm<<<1, 1, 0, ctx.stream>>>(scal, initial ? 0 : k, ctx.status.as<int>());
+    TRG_LAUNCHED(ctx);
+}
+
+void launch_init_ising3d(Ctx& ctx, double* T, double beta, double h) {
+    k_init_ising3d<<<1, 64, 0, ctx.stream>>>(T, beta, h);
+    TRG_LAUNCHED(ctx);
+}
+
+void launch_trace3(Ctx& ctx, const View6& t, double* slot) {
+    k_trace3<<<1, 256, 0, ctx.stream>>>(t.p, t.n[0], t.n[2], t.n[4], t.s[0] + t.s[1], t.s[2] + t.s[3],
+                                        t.s[4] + t.s[5], slot, ctx.status.as<int>());
     TRG_LAUNCHED(ctx);
 }
 

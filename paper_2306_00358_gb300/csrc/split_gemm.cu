@@ -951,22 +951,27 @@ __global__ void __launch_bounds__(256) k_row_exponent(const double* __restrict__
                                                       const int64_t* __restrict__ off_c, int R, int K, int k_fast,
                                                       int* __restrict__ ef_out) {
     __shared__ int rmax[SL_R];
-    const int r0 = blockIdx.y * SL_R, k0 = blockIdx.x * SL_K;
-    if (threadIdx.x < SL_R) rmax[threadIdx.x] = 0;
-    __syncthreads();
-    for (int e = threadIdx.x; e < SL_R * SL_K; e += 256) {
-        int rr, kk;
-        if (k_fast) { kk = e % SL_K; rr = e / SL_K; } else { rr = e % SL_R; kk = e / SL_R; }
-        const int r = r0 + rr, k = k0 + kk;
-        if (r < R && k < K) {
-            const unsigned long long b = (unsigned long long)__double_as_longlong(src[off_r[r] + off_c[k]]);
-            const int ef = (int)((b >> 52) & 0x7FF);
-            if (ef) atomicMax(&rmax[rr], ef);
+    const int k0 = blockIdx.x * SL_K;
+    const int nby = (R + SL_R - 1) / SL_R;   // row blocks, strided over grid.y (at most 65535)
+    for (int by = blockIdx.y; by < nby; by += gridDim.y) {
+        const int r0 = by * SL_R;
+        if (threadIdx.x < SL_R) rmax[threadIdx.x] = 0;
+        __syncthreads();
+        for (int e = threadIdx.x; e < SL_R * SL_K; e += 256) {
+            int rr, kk;
+            if (k_fast) { kk = e % SL_K; rr = e / SL_K; } else { rr = e % SL_R; kk = e / SL_R; }
+            const int r = r0 + rr, k = k0 + kk;
+            if (r < R && k < K) {
+                const unsigned long long b = (unsigned long long)__double_as_longlong(src[off_r[r] + off_c[k]]);
+                const int ef = (int)((b >> 52) & 0x7FF);
+                if (ef) atomicMax(&rmax[rr], ef);
+            }
         }
+        __syncthreads();
+        if (threadIdx.x < SL_R && r0 + (int)threadIdx.x < R && rmax[threadIdx.x])
+            atomicMax(&ef_out[r0 + threadIdx.x], rmax[threadIdx.x]);
+        __syncthreads();
     }
-    __syncthreads();
-    if (threadIdx.x < SL_R && r0 + (int)threadIdx.x < R && rmax[threadIdx.x])
-        atomicMax(&ef_out[r0 + threadIdx.x], rmax[threadIdx.x]);
 }
 
 // Convert the raw exponent fields to scale exponents e (|x| < 2^e).
@@ -982,47 +987,52 @@ __global__ void __launch_bounds__(256) k_slice(const double* __restrict__ src, c
                                                int k_fast, const int* __restrict__ e_row,
                                                uint16_t* __restrict__ out) {
     __shared__ double tile[SL_R][SL_K + 1];
-    const int r0 = blockIdx.y * SL_R, k0 = blockIdx.x * SL_K;
-    for (int e = threadIdx.x; e < SL_R * SL_K; e += 256) {
-        int rr, kk;
-        if (k_fast) { kk = e % SL_K; rr = e / SL_K; } else { rr = e % SL_R; kk = e / SL_R; }
-        const int r = r0 + rr, k = k0 + kk;
-        tile[rr][kk] = (r < R && k < K) ? src[off_r[r] + off_c[k]] : 0.0;
-    }
-    __syncthreads();
-    constexpr int F = 7 + 8 * (S - 1);
-    for (int e = threadIdx.x; e < SL_R * SL_K; e += 256) {
-        const int kk = e % SL_K, rr = e / SL_K;
-        const int r = r0 + rr, k = k0 + kk;
-        if (r >= Rp || k >= Kp) continue;
-        long long X = 0;
-        if (r < R) {
-            const unsigned long long b = (unsigned long long)__double_as_longlong(tile[rr][kk]);
-            const int ex = (int)((b >> 52) & 0x7FF);
-            if (ex) {
-                const int ea = e_row[r];                       // |x| < 2^ea
-                const int shift = 52 + 1023 + ea - ex - F;     // >= 53 - F > 0
-                if (shift < 63) {
-                    const unsigned long long m53 = (b & ((1ull << 52) - 1)) | (1ull << 52);
-                    X = (long long)((m53 + (1ull << (shift - 1))) >> shift);
-                    if (b >> 63) X = -X;
+    const int k0 = blockIdx.x * SL_K;
+    const int nby = (Rp + SL_R - 1) / SL_R;   // row blocks, strided over grid.y (at most 65535)
+    for (int by = blockIdx.y; by < nby; by += gridDim.y) {
+        const int r0 = by * SL_R;
+        __syncthreads();   // the previous block's tile has been read
+        for (int e = threadIdx.x; e < SL_R * SL_K; e += 256) {
+            int rr, kk;
+            if (k_fast) { kk = e % SL_K; rr = e / SL_K; } else { rr = e % SL_R; kk = e / SL_R; }
+            const int r = r0 + rr, k = k0 + kk;
+            tile[rr][kk] = (r < R && k < K) ? src[off_r[r] + off_c[k]] : 0.0;
+        }
+        __syncthreads();
+        constexpr int F = 7 + 8 * (S - 1);
+        for (int e = threadIdx.x; e < SL_R * SL_K; e += 256) {
+            const int kk = e % SL_K, rr = e / SL_K;
+            const int r = r0 + rr, k = k0 + kk;
+            if (r >= Rp || k >= Kp) continue;
+            long long X = 0;
+            if (r < R) {
+                const unsigned long long b = (unsigned long long)__double_as_longlong(tile[rr][kk]);
+                const int ex = (int)((b >> 52) & 0x7FF);
+                if (ex) {
+                    const int ea = e_row[r];                       // |x| < 2^ea
+                    const int shift = 52 + 1023 + ea - ex - F;     // >= 53 - F > 0
+                    if (shift < 63) {
+                        const unsigned long long m53 = (b & ((1ull << 52) - 1)) | (1ull << 52);
+                        X = (long long)((m53 + (1ull << (shift - 1))) >> shift);
+                        if (b >> 63) X = -X;
+                    }
                 }
             }
-        }
-        int d[S];
+            int d[S];
 #pragma unroll
-        for (int p = S - 1; p >= 1; --p) {
-            const int lo = (int)(((X + 128) & 255) - 128);
-            d[p] = lo;
-            X = (X - lo) >> 8;
-        }
-        d[0] = (int)X;
-        const size_t plane = (size_t)Rp * Kp;
+            for (int p = S - 1; p >= 1; --p) {
+                const int lo = (int)(((X + 128) & 255) - 128);
+                d[p] = lo;
+                X = (X - lo) >> 8;
+            }
+            d[0] = (int)X;
+            const size_t plane = (size_t)Rp * Kp;
 #pragma unroll
-        for (int p = 0; p < S; ++p) {
-            // small integer -> FP32 exactly (|d| < 2^22), times 2^-8p, top 16 bits = BF16
-            const float f = (__int_as_float(0x4B400000 + d[p]) - 12582912.0f) * __int_as_float((127 - 8 * p) << 23);
-            out[p * plane + (size_t)r * Kp + k] = (uint16_t)(__float_as_uint(f) >> 16);
+            for (int p = 0; p < S; ++p) {
+                // small integer -> FP32 exactly (|d| < 2^22), times 2^-8p, top 16 bits = BF16
+                const float f = (__int_as_float(0x4B400000 + d[p]) - 12582912.0f) * __int_as_float((127 - 8 * p) << 23);
+                out[p * plane + (size_t)r * Kp + k] = (uint16_t)(__float_as_uint(f) >> 16);
+            }
         }
     }
 }
@@ -1222,14 +1232,14 @@ void launch_slice(Ctx& ctx, const Gather& g, int R, int K, int Rp, int Kp, const
         TRG_LAUNCHED(ctx);
         return;
     }
-    dim3 grid((unsigned)((Kp + SL_K - 1) / SL_K), (unsigned)((Rp + SL_R - 1) / SL_R));
+    dim3 grid((unsigned)((Kp + SL_K - 1) / SL_K), (unsigned)std::min<int64_t>((Rp + SL_R - 1) / SL_R, 65535));
     k_slice<S><<<grid, 256, 0, ctx.stream>>>(g.base, g.off_r, g.off_c, R, K, Rp, Kp, g.c_fast ? 1 : 0, e, out);
     TRG_LAUNCHED(ctx);
 }
 
 void row_exponents(Ctx& ctx, const Gather& g, int R, int K, int* e) {
     TRG_CUDA(cudaMemsetAsync(e, 0, (size_t)R * sizeof(int), ctx.stream));
-    dim3 grid((unsigned)((K + SL_K - 1) / SL_K), (unsigned)((R + SL_R - 1) / SL_R));
+    dim3 grid((unsigned)((K + SL_K - 1) / SL_K), (unsigned)std::min<int64_t>((R + SL_R - 1) / SL_R, 65535));
     k_row_exponent<<<grid, 256, 0, ctx.stream>>>(g.base, g.off_r, g.off_c, R, K, g.c_fast ? 1 : 0, e);
     TRG_LAUNCHED(ctx);
     k_exponent_finish<<<(unsigned)((R + 255) / 256), 256, 0, ctx.stream>>>(e, R);
@@ -1460,15 +1470,15 @@ extern "C" int trg_gemm_noalloc(int M, int N, int K, const double* A, int lda, c
 
         // row exponents and slices of A (rows m, k contiguous) and of B as (n, k)
         {
-            dim3 ga((unsigned)((K + SL_K - 1) / SL_K), (unsigned)((M + SL_R - 1) / SL_R));
+            dim3 ga((unsigned)((K + SL_K - 1) / SL_K), (unsigned)std::min<int64_t>((M + SL_R - 1) / SL_R, 65535));
             k_row_exponent<<<ga, 256, 0, stream>>>(A, am, ak, M, K, 1, ea);
-            dim3 gb((unsigned)((K + SL_K - 1) / SL_K), (unsigned)((N + SL_R - 1) / SL_R));
+            dim3 gb((unsigned)((K + SL_K - 1) / SL_K), (unsigned)std::min<int64_t>((N + SL_R - 1) / SL_R, 65535));
             k_row_exponent<<<gb, 256, 0, stream>>>(B, bn, bk, N, K, 0, eb);
             k_exponent_finish<<<(unsigned)((M + 255) / 256), 256, 0, stream>>>(ea, M);
             k_exponent_finish<<<(unsigned)((N + 255) / 256), 256, 0, stream>>>(eb, N);
             TRG_CUDA(cudaGetLastError());
-            dim3 sa_grid((unsigned)((Kp + SL_K - 1) / SL_K), (unsigned)(Mp / SL_R));
-            dim3 sb_grid((unsigned)((Kp + SL_K - 1) / SL_K), (unsigned)(Np / SL_R));
+            dim3 sa_grid((unsigned)((Kp + SL_K - 1) / SL_K), (unsigned)std::min<int64_t>(Mp / SL_R, 65535));
+            dim3 sb_grid((unsigned)((Kp + SL_K - 1) / SL_K), (unsigned)std::min<int64_t>(Np / SL_R, 65535));
             switch (S) {
                 case 2: k_slice<2><<<sa_grid, 256, 0, stream>>>(A, am, ak, M, K, Mp, Kp, 1, ea, sa);
                         k_slice<2><<<sb_grid, 256, 0, stream>>>(B, bn, bk, N, K, Np, Kp, 0, eb, sb); break;

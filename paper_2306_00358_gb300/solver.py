@@ -150,6 +150,14 @@ class Solver:
         self._check(self._lib.trg_free_energy(self._h, ctypes.byref(f), ctypes.byref(lnz)), "trg_free_energy")
         return f.value, lnz.value
 
+    def solve3d(self, beta: float, h: float, dcut: int, nsteps: int, model: str = "ising"):
+        """A whole cubic-lattice solve (steps z, x, y, ...): returns (f, ln Z / V)."""
+        f = ctypes.c_double()
+        lnz = ctypes.c_double()
+        self._check(self._lib.trg_solve3d(self._h, _MODELS[model.lower()], float(beta), float(h), int(dcut),
+                                          int(nsteps), ctypes.byref(f), ctypes.byref(lnz)), "trg_solve3d")
+        return f.value, lnz.value
+
     def spectrum(self, step: int) -> np.ndarray:
         n = ctypes.c_int()
         self._check(self._lib.trg_get_spectrum(self._h, int(step), None, 0, ctypes.byref(n)), "trg_get_spectrum")
