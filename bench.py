@@ -197,8 +197,8 @@ def load_peaks():
 # of two timed half-steps of this workload, from the ncu capture summarised in
 # profiles/split_mma_dram_hotrg_ising_dcut64_s4.md.  The figure describes the
 # kernel source it was taken on: reported only while that file is unchanged.
-SPLIT_MMA_TRAFFIC = {"sha256": "7123b777a8ec7c5016ed1c796690d857b6525c0d0d484c7676a991bad5925b59",
-                     "bytes_per_launch": 5.408e9}
+SPLIT_MMA_TRAFFIC = {"sha256": "2475ac5722860b238e0824d84d4a7169a06d81256e3d479923d28ce73512803f",
+                     "bytes_per_launch": 5.522e9}
 
 
 def split_mma_traffic():
