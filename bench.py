@@ -88,7 +88,10 @@ class ClockSampler:
     def __init__(self, index: int):
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
+        # raw samples (the JSON line carries their summary): TRG_BENCH_OUT, else the temp directory
+        import tempfile
+        out_dir = os.environ.get("TRG_BENCH_OUT") or tempfile.gettempdir()
+        self.path = os.path.join(out_dir, f"trg_clocks_rank{index}.csv")
 
     def start(self):
         try:
