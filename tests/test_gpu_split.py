@@ -48,6 +48,20 @@ def test_split_gemm_exact_on_integers(torch, m, n, k, s):
     assert np.array_equal(c, ref)
 
 
+@pytest.mark.parametrize("m,n", [(2_200_000, 3), (3, 2_200_000)])
+def test_split_gemm_exact_with_many_rows(torch, m, n):
+    # more than 65535 x 32 rows in one operand: the exponent and slicing
+    # kernels stride over their row blocks instead of one block per row group
+    k = 40
+    rng = np.random.default_rng(m + n)
+    a = rng.integers(-100, 101, size=(m, k)).astype(np.float64)
+    b = rng.integers(-100, 101, size=(k, n)).astype(np.float64)
+    ref = a @ b
+    with Solver(0, precision="split", split_slices=4) as sv:
+        c = sv.gemm(torch.from_numpy(a).cuda(), torch.from_numpy(b).cuda()).cpu().numpy()
+    assert np.array_equal(c, ref)
+
+
 @pytest.mark.parametrize("m,n,k", [(200, 300, 4096), (129, 64, 777), (512, 80, 4096)])
 @pytest.mark.parametrize("s", [2, 3, 4, 5])
 def test_split_gemm_error_bound(torch, m, n, k, s):
