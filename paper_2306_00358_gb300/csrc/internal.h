@@ -94,7 +94,7 @@ struct Ctx {
     Buf f64_partial;       // FP64 GEMM: split-K partial sums
     Buf cons_ef;           // exponent fields recorded by a producing product (two halves)
     Buf eig_slices;        // split mode: M sliced once per isometry solve
-    Buf s3[10];            // cubic-lattice step: P1, P2, Mx, My, Ux, Uy and the contraction intermediates
+    Buf s3[10];            // cubic-lattice step: P1, P2, Ux, Uy, Mx, My, then A, W, C, D of the contraction
     std::map<std::string, Buf> tables;  // cached offset tables
 
     // ---- phase timing
