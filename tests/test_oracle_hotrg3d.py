@@ -37,13 +37,23 @@ def test_single_site_trace():
 
 
 def test_enumeration_known_cases():
-    # beta = 0: Z = 2^V; h only: Z = (2 cosh(beta h))^V with beta = 1
+    # beta = 0: Z = 2^V
     assert exact.ising3d_lnz_exact(2, 1, 2, 0.0) == pytest.approx(4 * math.log(2), abs=1e-13)
     # a 2x1x1 ring with bonds in x (two between the sites) and self-bonds in y, z:
     # Z = sum_{s1,s2} e^{2 beta s1 s2 + 4 beta} = 2 e^{4b} (e^{2b} + e^{-2b})
     b = 0.37
     ref = math.log(2 * math.exp(4 * b) * (math.exp(2 * b) + math.exp(-2 * b)))
     assert exact.ising3d_lnz_exact(2, 1, 1, b) == pytest.approx(ref, abs=1e-13)
+
+
+def test_site_tensor_leg_symmetry():
+    # every leg carries the same W row of the site spin, so the tensor is
+    # invariant under all 720 leg permutations (field included), up to the
+    # rounding of the six-factor products taken in different orders
+    import itertools
+    t = hotrg3d.ising3d_tensor(0.31, 0.2)
+    for perm in itertools.permutations(range(6)):
+        assert np.abs(t - t.transpose(perm)).max() <= 4e-16 * np.abs(t).max()
 
 
 def _stack(t):
