@@ -40,6 +40,11 @@ def parse():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--precision", default=None, choices=["split", "fp64"])
     ap.add_argument("--slices", type=int, default=4)
+    ap.add_argument("--env-slices", type=int, default=None,
+                    help="slices of the environment and isometry products (default: the contraction's)")
+    ap.add_argument("--no-accuracy", action="store_true",
+                    help="skip the headline accuracy leg (split and FP64 solves of the Dcut-64 beta_c workload)")
+    ap.add_argument("--no-calibration", action="store_true", help="skip the in-run calibration products")
     ap.add_argument("--fused-slices", type=int, default=1, choices=[0, 1, 2],
                     help="slice hand-over between contraction products: none (0), D^7 -> last (1), all (2)")
     ap.add_argument("--mma-pairs", type=int, default=0, choices=[0, 1],
@@ -196,12 +201,18 @@ def load_peaks():
         return {}
 
 
-# DRAM bytes (read + write) per k_split_mma launch, averaged over the launches
-# of two timed half-steps of this workload, from the ncu capture summarised in
-# profiles/split_mma_dram_hotrg_ising_dcut64_s4.md.  The figure describes the
-# kernel source it was taken on: reported only while that file is unchanged.
-SPLIT_MMA_TRAFFIC = {"sha256": "2475ac5722860b238e0824d84d4a7169a06d81256e3d479923d28ce73512803f",
-                     "bytes_per_launch": 5.522e9}
+# DRAM bytes (read + write) per launch of the D^7 product's k_split_mma
+# (X2 = X1.t, one j-block of 16 at Dcut 64), from an ncu capture of that
+# kernel in this workload (the profiles directory holds its summary).  The
+# figure describes the kernel source it was taken on: reported only while
+# that file is unchanged, else null.
+SPLIT_MMA_TRAFFIC = {"sha256": None, "bytes_per_launch": None}
+# Algorithmic bytes of one X2 launch at Dcut 64, S = 4: read the A slices
+# (S x 65536 x 4096 BF16) and the B slices (S x 4096 x 4096 BF16), write the
+# next product's A slices (S x 65536 x 4096 BF16) and row exponents.
+def x2_algorithmic_bytes(slices: int, d: int = DCUT, jb: int = 16) -> float:
+    rows = jb * d * d
+    return float(slices * rows * d * d * 2 + slices * d * d * d * d * 2 + slices * rows * d * d * 2 + rows * 8)
 
 
 def split_mma_traffic():
@@ -212,7 +223,103 @@ def split_mma_traffic():
             digest = hashlib.sha256(f.read()).hexdigest()
     except OSError:
         return None
+    if SPLIT_MMA_TRAFFIC["sha256"] is None:
+        return None
     return SPLIT_MMA_TRAFFIC["bytes_per_launch"] if digest == SPLIT_MMA_TRAFFIC["sha256"] else None
+
+
+def calibration(slices: int):
+    """Products timed in the same run as the bench line: a plain BF16 matmul
+    (torch, 8192^3, best of 5), an HBM copy (1 GiB, best of 5) and the split
+    product 16384 x 4096 x 4096 (the library's own kernel, tensor-core rate of
+    its slice products)."""
+    import torch
+
+    from paper_2306_00358_gb300 import Solver
+
+    out = {}
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    n = 8192
+    a = torch.randn(n, n, device="cuda", dtype=torch.bfloat16)
+    b = torch.randn(n, n, device="cuda", dtype=torch.bfloat16)
+    for _ in range(3):
+        torch.matmul(a, b)
+    best = 1e30
+    for _ in range(5):
+        ev0.record()
+        torch.matmul(a, b)
+        ev1.record()
+        torch.cuda.synchronize()
+        best = min(best, ev0.elapsed_time(ev1))
+    out["bf16_matmul_8192_tflops"] = 2.0 * n ** 3 / (best / 1e3) / 1e12
+    del a, b
+    src = torch.empty(1 << 30, device="cuda", dtype=torch.bfloat16)
+    dst = torch.empty_like(src)
+    dst.copy_(src)
+    best = 1e30
+    for _ in range(5):
+        ev0.record()
+        dst.copy_(src)
+        ev1.record()
+        torch.cuda.synchronize()
+        best = min(best, ev0.elapsed_time(ev1))
+    out["hbm_copy_gbs"] = 2.0 * src.numel() * 2 / (best / 1e3) / 1e9
+    del src, dst
+    import numpy as np
+    rng = np.random.default_rng(3)
+    m, nn, k = 16384, 4096, 4096
+    x = torch.from_numpy(rng.standard_normal((m, k))).cuda()
+    y = torch.from_numpy(rng.standard_normal((k, nn))).cuda()
+    with Solver(0, precision="split", split_slices=slices) as s:
+        s.gemm(x, y)
+        s.profile(True)
+        for _ in range(3):
+            s.gemm(x, y)
+        mma = s.phase_stats()["mma"]
+        s.profile(False)
+    t = mma["ms"] / max(1, mma["calls"]) / 1e3
+    out["split_gemm_16384x4096x4096"] = {"slices": slices, "mma_ms": t * 1e3,
+                                         "slice_tflops": mma["mma_flops"] / max(1, mma["calls"]) / t / 1e12,
+                                         "fp64_equiv_tflops": 2.0 * m * nn * k / t / 1e12}
+    torch.cuda.synchronize()
+    return out
+
+
+def accuracy_leg(slices: int, env_slices, dcut: int = DCUT, beta: float = BETA_C, h: float = 1e-3,
+                 nsteps: int = 40):
+    """The headline gate: the same solve (2D Ising, Dcut 64, beta_c, h = 1e-3,
+    40 half-steps) in split precision and in plain FP64 on the GPU; |f_split -
+    f_fp64| and the seconds per steady-state half-step of each path (CUDA
+    events over half-steps 7..40, where Dx = Dy = Dcut)."""
+    import torch
+
+    from paper_2306_00358_gb300 import Solver
+
+    out = {"workload": f"2D Ising, beta_c, h={h:g}, Dcut={dcut}, {nsteps} half-steps", "slices": slices,
+           "env_slices": env_slices or slices}
+    for prec in ("split", "fp64"):
+        kw = {"split_slices": slices}
+        if env_slices:
+            kw["env_slices"] = env_slices
+        stream = torch.cuda.current_stream()
+        t0 = time.perf_counter()
+        with Solver(0, stream=stream, precision=prec, **kw) as s:
+            s.init_tensor("ising", beta, h)
+            s.coarse_grain(dcut, STEADY_AT)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            s.coarse_grain(dcut, nsteps - STEADY_AT)
+            e1.record(stream)
+            f, _ = s.free_energy()
+            torch.cuda.synchronize()
+        out[f"f_{prec}"] = f
+        out[f"{prec}_s_per_step"] = e0.elapsed_time(e1) / 1e3 / (nsteps - STEADY_AT)
+        out[f"{prec}_solve_s"] = time.perf_counter() - t0
+    out["abs_df"] = abs(out["f_split"] - out["f_fp64"])
+    out["gate"] = 1e-9
+    out["pass"] = out["abs_df"] <= 1e-9
+    out["speedup_split_vs_fp64_per_step"] = out["fp64_s_per_step"] / out["split_s_per_step"]
+    return out
 
 
 def replica_beta(rank: int) -> float:
@@ -259,8 +366,9 @@ def run_native(args):
         torch.cuda.synchronize()
 
     stream = torch.cuda.current_stream()
+    extra = {"env_slices": args.env_slices} if args.env_slices else {}
     s = Solver(local, stream=stream, precision=precision, split_slices=args.slices, mma_pairs=args.mma_pairs,
-               fused_slices=args.fused_slices)
+               fused_slices=args.fused_slices, **extra)
     beta = replica_beta(rank)
     s.init_tensor("ising", beta, 0.0)
     s.coarse_grain(DCUT, STEADY_AT)
@@ -303,14 +411,25 @@ def run_native(args):
                 "traffic": None, "kernel": "k_gemm_f64 (X2 = X1.t, D^7)",
                 "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x max SM clock"}
     else:
-        mma = ph["mma"]
-        per_launch = mma["mma_flops"] / max(1, mma["calls"])
-        t_launch = mma["ms"] / max(1, mma["calls"]) / 1e3
+        # the X2 product's tensor-core launches alone (events around each launch)
+        mx = ph["mma_x2"]
+        calls = max(1, mx["calls"])
+        per_launch = mx["mma_flops"] / calls          # slice-product FLOPs of one launch
+        t_launch = mx["ms"] / calls / 1e3
         achieved = per_launch / t_launch / 1e12 if t_launch > 0 else 0.0
-        peak = peaks.get("bf16_tflops_sustained", 1722.5)
+        peak = peaks.get("bf16_tflops_sustained", 1713.4)
+        products = args.slices * (args.slices + 1) / 2
+        traffic = split_mma_traffic()
+        alg = x2_algorithmic_bytes(args.slices)
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": split_mma_traffic(), "kernel": "k_split_mma (BF16 slice products)",
-                "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained (of measured)"}
+                "frac": achieved / peak, "traffic": traffic,
+                "kernel": "k_split_mma<%d,1,EPI_FUSED> (X2 = X1.t, the D^7 product)" % args.slices,
+                "launches_per_step": mx["calls"] / steps, "ms_per_launch": t_launch * 1e3,
+                "fp64_equiv_tflops": mx["flops"] / calls / t_launch / 1e12 if t_launch > 0 else 0.0,
+                "split_roofline_fp64_equiv": peak / products,
+                "algorithmic_bytes": alg, "traffic_over_algorithmic": traffic / alg if traffic else None,
+                "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained (of measured); achieved counts the "
+                               "S(S+1)/2 BF16 slice products"}
 
     # end to end through the C ABI with host buffers
     e2e = None
@@ -343,6 +462,14 @@ def run_native(args):
         f, _ = s.free_energy()
         solve = {"seconds": time.perf_counter() - t0, "solves_per_s": 1.0 / (time.perf_counter() - t0), "f": f}
 
+    calib = None
+    if rank == 0 and world == 1 and not args.no_calibration:
+        calib = calibration(args.slices)
+        calib["measured_peaks_json"] = {k: peaks.get(k) for k in ("hbm_gbs", "bf16_tflops", "bf16_tflops_sustained")}
+    acc = None
+    if rank == 0 and world == 1 and not args.no_accuracy and precision == "split":
+        acc = accuracy_leg(args.slices, args.env_slices)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         v, desc = oracle_half_step_sample()
@@ -357,7 +484,11 @@ def run_native(args):
                            "l2": "inputs larger than L2 (T 134 MB, M 134 MB, workspace >= 1 GB per step)",
                            "parallelism": "replicas" if world > 1 else "single"},
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
-                "phases_ms": {k: round(v["ms"], 3) for k, v in ph.items()}, "counters": counters, "solve": solve}
+                "phases_ms": {k: round(v["ms"], 3) for k, v in ph.items()}, "counters": counters, "solve": solve,
+                "calibration": calib, "accuracy": acc}
+        if acc:
+            line.update({"f_split": acc["f_split"], "f_fp64": acc["f_fp64"], "abs_df": acc["abs_df"],
+                         "fp64_s_per_step": acc["fp64_s_per_step"]})
         print(json.dumps(line), flush=True)
     s.close()
     if world > 1:
@@ -441,7 +572,8 @@ def run_sweep(args):
                 for prec, slices in precs:
                     torch.cuda.synchronize()
                     t0 = time.perf_counter()
-                    with Solver(0, precision=prec, split_slices=slices, trunc=trunc) as s:
+                    extra = {"env_slices": args.env_slices} if (args.env_slices and prec == "split") else {}
+                    with Solver(0, precision=prec, split_slices=slices, trunc=trunc, **extra) as s:
                         s.init_tensor(args.sweep_model, beta, h)
                         s.coarse_grain(dcut, nsteps)
                         f, _ = s.free_energy()
@@ -457,7 +589,8 @@ def run_sweep(args):
                 print(json.dumps(rec), flush=True)
                 out.append(rec)
     dfs = [r["abs_df_split_fp64"] for r in out if "abs_df_split_fp64" in r]
-    print(json.dumps({"mode": "sweep", "model": args.sweep_model, "slices": args.slices, "runs": len(out),
+    print(json.dumps({"mode": "sweep", "model": args.sweep_model, "slices": args.slices,
+                      "env_slices": args.env_slices or args.slices, "runs": len(out),
                       "max_abs_df_split_fp64": max(dfs) if dfs else None}), flush=True)
 
 

@@ -67,14 +67,15 @@ typedef enum trg_trunc {
 
 typedef struct trg_config {
     int precision;           /* trg_precision (default TRG_FP64) */
-    int split_slices;        /* BF16 slices per operand in TRG_SPLIT_BF16, 2..5 (default 4) */
+    int split_slices;        /* BF16 slices per operand in TRG_SPLIT_BF16, 2..5 (default 4);
+                                the contraction products use it (see env_slices) */
     int split_from_step;     /* half-steps with index < this run in FP64 (default 0) */
     int trunc;               /* trg_trunc (default TRG_TRUNC_PAPER) */
     double gap_tol;          /* multiplet gap, relative to lambda_1 (default 1e-6; in
-                                TRG_SPLIT_BF16 at least 2^-(8*split_slices-12)) */
+                                TRG_SPLIT_BF16 at least 2^-(8*S-12), S = the env slices) */
     int oversample;          /* subspace-iteration oversampling p (default 24; at most 112 - Dcut) */
     double eig_tol;          /* Ritz residual tolerance relative to lambda_1 (default 1e-12; in
-                                TRG_SPLIT_BF16 at least 2^-(8*split_slices-10)) */
+                                TRG_SPLIT_BF16 at least 2^-(8*S-10), S = the env slices) */
     int eig_max_iter;        /* subspace iterations before TRG_ENUMERIC (default 300) */
     uint64_t seed;           /* seed of the start block of the subspace iteration */
     size_t workspace_bytes;  /* bound on the contraction workspace (0 = 4 GiB) */
@@ -88,6 +89,9 @@ typedef struct trg_config {
                                 slicing pass); 2 also hands the first product over as
                                 slices; 0 always goes through FP64.  Results are identical
                                 in all three. */
+    int env_slices;          /* TRG_SPLIT_BF16: BF16 slices of the environment products and of
+                                the isometry's M.Q products, 2..5; 0 (default) = split_slices.
+                                The isometry's tolerances above then follow env_slices. */
 } trg_config;
 
 typedef struct trg_ctx trg_ctx;
@@ -276,8 +280,10 @@ int trg_gemm(trg_ctx* ctx, int M, int N, int K, const double* A_dev, int lda, co
  *   - The first call on a device looks up the array's device address
  *     (cudaGetSymbolAddress); make that first call before any stream capture.
  *   - Every call shares the one array: calls that overlap on the GPU (other
- *     threads, other streams) race and corrupt each other's results.  The
- *     call waits for its own work to finish before returning.
+ *     threads, other streams) race and corrupt each other's results.
+ *   - Every call copies its status word to the host and synchronises
+ *     `stream` before it returns, so it blocks until its own work is done.
+ *   - M and N above 2^30 or K above 131072 are rejected with TRG_EINVAL.
  * Returns TRG_OK, TRG_EINVAL, TRG_ENOTSUP (not a GB300), TRG_ETIMEOUT or
  * TRG_ECUDA.
  */
@@ -382,7 +388,8 @@ typedef enum trg_phase {
     TRG_PHASE_X3 = 4,     /* Tx = X2.U       (D^6) */
     TRG_PHASE_NORM = 5,   /* max-abs normalisation and log-norm */
     TRG_PHASE_MMA = 6,    /* split mode: the tensor-core kernels alone (all products) */
-    TRG_PHASE_COUNT = 7
+    TRG_PHASE_MMA_X2 = 7, /* split mode: the tensor-core kernel launches of the X2 product alone */
+    TRG_PHASE_COUNT = 8
 } trg_phase;
 
 typedef struct trg_phase_stats {

@@ -41,6 +41,7 @@ class trg_config(ctypes.Structure):
         ("workspace_bytes", c_size_t),
         ("mma_pairs", c_int),
         ("fused_slices", c_int),
+        ("env_slices", c_int),
     ]
 
 
@@ -48,7 +49,7 @@ class trg_phase_stats(ctypes.Structure):
     _fields_ = [("ms", c_double), ("calls", c_uint64), ("flops", c_double), ("mma_flops", c_double)]
 
 
-PHASES = ("env", "eig", "x1", "x2", "x3", "norm", "mma")
+PHASES = ("env", "eig", "x1", "x2", "x3", "norm", "mma", "mma_x2")
 TRG_EAGAIN, TRG_ECANCELED = 8, 9
 TRG_SERVE_FIFO, TRG_SERVE_SHORTEST_FIRST = 0, 1
 TRG_DRY_RUN_FAIL_SEED = 0xFA17FA17

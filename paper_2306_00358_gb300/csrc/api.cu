@@ -256,12 +256,14 @@ int trg_config_default(trg_config* cfg) {
     cfg->workspace_bytes = 0;
     cfg->mma_pairs = 0;
     cfg->fused_slices = 1;
+    cfg->env_slices = 0;
     return TRG_OK;
 }
 
 static int validate_config(const trg_config& c) {
     if (c.precision != TRG_FP64 && c.precision != TRG_SPLIT_BF16) return TRG_EINVAL;
     if (c.split_slices < 2 || c.split_slices > 5) return TRG_EINVAL;
+    if (c.env_slices != 0 && (c.env_slices < 2 || c.env_slices > 5)) return TRG_EINVAL;
     if (c.split_from_step < 0) return TRG_EINVAL;
     if (c.mma_pairs != 0 && c.mma_pairs != 1) return TRG_EINVAL;
     if (c.fused_slices < 0 || c.fused_slices > 2) return TRG_EINVAL;
@@ -602,6 +604,7 @@ int trg_environment(trg_ctx* ctx, const double* t_dev, int Dx, int Dy, double* M
     TRG_GUARD_BEGIN
     TRG_CUDA(cudaSetDevice(ctx->device));
     trg::View4 t = trg::contiguous_view(const_cast<double*>(t_dev), Dx, Dy, Dx, Dy);
+    ctx->phase = TRG_PHASE_ENV;
     trg::environment(*ctx, t, M_dev, ctx->cfg.precision);
     TRG_CUDA(cudaStreamSynchronize(ctx->stream));
     return TRG_OK;
@@ -620,6 +623,7 @@ int trg_isometry(trg_ctx* ctx, const double* M_dev, int n, int Dcut, double* U_d
     } else {
         std::vector<double> lam;
         ctx->eig_hint[1] = trg::Ctx::EigHint();   // a component call starts from scratch
+        ctx->phase = TRG_PHASE_EIG;
         const int dn = trg::isometry(*ctx, M_dev, n, Dcut, U_dev, lam, 1, ctx->cfg.precision);
         *dn_out = dn;
         if (lam_host) std::memcpy(lam_host, lam.data(), sizeof(double) * (size_t)dn);
@@ -637,6 +641,7 @@ int trg_contract(trg_ctx* ctx, const double* t_dev, const double* U_dev, int Dx,
     TRG_CUDA(cudaSetDevice(ctx->device));
     trg::View4 t = trg::contiguous_view(const_cast<double*>(t_dev), Dx, Dy, Dx, Dy);
     trg::View4 o = trg::contiguous_view(Tx_dev, Dn, Dy, Dn, Dy);
+    ctx->phase = TRG_PHASE_X1;
     trg::contract(*ctx, t, t, U_dev, Dn, o, ctx->cfg.precision);
     TRG_CUDA(cudaStreamSynchronize(ctx->stream));
     return TRG_OK;

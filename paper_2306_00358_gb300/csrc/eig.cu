@@ -582,7 +582,7 @@ int isometry(Ctx& ctx, const double* M, int64_t n, int dcut, double* U, std::vec
     const uint16_t* m_slices = nullptr;
     const int* m_e = nullptr;
     if (precision == TRG_SPLIT_BF16) {
-        const size_t sl = (size_t)ctx.cfg.split_slices * split_rows_padded(ctx, n) * split_k_padded(n) * 2;
+        const size_t sl = (size_t)slices_now(ctx) * split_rows_padded(ctx, n) * split_k_padded(n) * 2;
         const size_t eb = (size_t)split_rows_padded(ctx, n) * sizeof(int);
         ctx.ensure(ctx.eig_slices, sl + eb + 256);
         uint16_t* sp = ctx.eig_slices.as<uint16_t>();
@@ -624,7 +624,8 @@ int isometry(Ctx& ctx, const double* M, int64_t n, int dcut, double* U, std::vec
     // residual; f is insensitive to residuals far above that floor (1e-6
     // moves f by ~1e-12 on the Ising workloads), so stop at 2^-(8S-10).
     double tol = ctx.cfg.eig_tol;
-    if (precision == TRG_SPLIT_BF16) tol = std::max(tol, std::ldexp(1.0, -(8 * ctx.cfg.split_slices - 10)));
+    const int S_env = slices_now(ctx);   // the slices of this solve's M.Q products
+    if (precision == TRG_SPLIT_BF16) tol = std::max(tol, std::ldexp(1.0, -(8 * S_env - 10)));
     std::vector<double> th((size_t)m);
     const int max_it = std::max(1, ctx.cfg.eig_max_iter);
     // Rayleigh-Ritz is the costly part (a one-SM Jacobi solve), so it is not
@@ -693,7 +694,7 @@ int isometry(Ctx& ctx, const double* M, int64_t n, int dcut, double* U, std::vec
                 // to ~2^-(8S-12) lambda_1: treat smaller gaps as degenerate
                 double gtol = ctx.cfg.gap_tol;
                 if (precision == TRG_SPLIT_BF16)
-                    gtol = std::max(gtol, std::ldexp(1.0, -(8 * ctx.cfg.split_slices - 12)));
+                    gtol = std::max(gtol, std::ldexp(1.0, -(8 * S_env - 12)));
                 while (dn > 1 && (th[(size_t)dn - 1] - th[(size_t)dn]) < gtol * th[0]) --dn;
             }
             lam.assign(th.begin(), th.begin() + dn);

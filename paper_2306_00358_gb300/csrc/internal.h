@@ -201,6 +201,9 @@ std::vector<int64_t> build_table(const std::vector<std::pair<int64_t, int64_t>>&
 
 // ------------------------------------------------------ path pieces ----
 int precision_for_step(const Ctx& ctx, int step);
+// BF16 slices of the split products issued now: env_slices during the
+// environment and the isometry (when set), split_slices otherwise.
+int slices_now(const Ctx& ctx);
 void environment(Ctx& ctx, const View4& t, double* M, int precision);
 // Tx = U . top . bottom . U (the upper tensor of the blocked pair is `top`,
 // the lower one `bottom`; both the same tensor for the pure half-step).

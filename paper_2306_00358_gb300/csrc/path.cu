@@ -71,6 +71,11 @@ void gemm(Ctx& ctx, const GemmDesc& g, int precision) {
     ctx.region_end(tok, 2.0 * (double)g.M * (double)g.N * (double)g.K, 0.0);
 }
 
+int slices_now(const Ctx& ctx) {
+    const bool env = ctx.phase == TRG_PHASE_ENV || ctx.phase == TRG_PHASE_EIG;
+    return (env && ctx.cfg.env_slices) ? ctx.cfg.env_slices : ctx.cfg.split_slices;
+}
+
 int precision_for_step(const Ctx& ctx, int step) {
     if (ctx.cfg.precision == TRG_FP64) return TRG_FP64;
     return (step - 1 < ctx.cfg.split_from_step) ? TRG_FP64 : ctx.cfg.precision;

@@ -1262,7 +1262,7 @@ static Gather transpose_gather(const Gather& b, const int64_t* off_k, const int6
 // reads (rows padded per split_rows_padded, K per split_k_padded), for a
 // caller that reuses one A across several products.
 void split_slice_operand(Ctx& ctx, const Gather& A, int64_t M, int64_t K, uint16_t* slices, int* e) {
-    const int S = ctx.cfg.split_slices;
+    const int S = slices_now(ctx);
     const int Mi = (int)M, Ki = (int)std::max<int64_t>(K, 1);
     const int Mp = (int)split_rows_padded(ctx, M), Kp = (int)split_k_padded(K);
     row_exponents(ctx, A, Mi, Ki, e);
@@ -1285,7 +1285,7 @@ void gemm_split(Ctx& ctx, const GemmDesc& d) {
     if (d.M <= 0 || d.N <= 0) return;
     if (d.beta != 0.0) fail(TRG_EINVAL, "split GEMM overwrites its output (beta must be 0)");
     if (d.M > (1ll << 30) || d.N > (1ll << 30) || d.K > (1 << 17)) fail(TRG_EINVAL, "split GEMM: size out of range");
-    const int S = ctx.cfg.split_slices;
+    const int S = slices_now(ctx);
     const int M = (int)d.M, N = (int)d.N, K = (int)std::max<int64_t>(d.K, 1);
     // CTA pairs (256-row tiles) once A has more than one 128-row block
     const int CG = (ctx.cfg.mma_pairs && M > BM) ? 2 : 1;
@@ -1352,6 +1352,7 @@ void gemm_split(Ctx& ctx, const GemmDesc& d) {
         if (!shape_ok) fail(TRG_EINVAL, "fused slice hand-over: consumer rows do not tile");
     }
     const int tok = ctx.region_begin(TRG_PHASE_MMA);
+    const int tok_x2 = ctx.phase == TRG_PHASE_X2 ? ctx.region_begin(TRG_PHASE_MMA_X2) : -1;
     switch (S * 2 + CG - 1) {
         case 4: launch_mma<2, 1>(ctx, ta, tb, a); break;
         case 5: launch_mma<2, 2>(ctx, ta, tb, a); break;
@@ -1363,6 +1364,7 @@ void gemm_split(Ctx& ctx, const GemmDesc& d) {
         case 11: launch_mma<5, 2>(ctx, ta, tb, a); break;
     }
     const double products = (double)S * (S + 1) / 2;
+    ctx.region_end(tok_x2, 2.0 * (double)M * N * K, products * 2.0 * (double)M * N * Kp);
     ctx.region_end(tok, 2.0 * (double)M * N * K, products * 2.0 * (double)M * N * Kp);
 }
 
@@ -1405,6 +1407,8 @@ extern "C" int trg_gemm_noalloc(int M, int N, int K, const double* A, int lda, c
     using namespace trg;
     if (!A || !B || !C || M < 1 || N < 1 || K < 1 || lda < K || ldb < N || ldc < N) return TRG_EINVAL;
     if (slices < 2 || slices > 5 || K > (1 << 17)) return TRG_EINVAL;
+    // the padded sizes below are ints: bound M and N first (as trg_gemm does)
+    if (M > (1 << 30) || N > (1 << 30)) return TRG_EINVAL;
     const int S = slices;
     const int Mp = (M + BM - 1) / BM * BM, Np = (N + BN - 1) / BN * BN, Kp = (K + BK - 1) / BK * BK;
     // layout of the scratch array

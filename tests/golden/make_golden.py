@@ -86,9 +86,44 @@ def expectations():
     print("wrote oracle_expectations.json")
 
 
+# The Ising coupling grid at Dcut 32 (beta_c, 0.40, 0.48 x h 0, 1e-3; 40
+# half-steps): the sizes of the split-versus-FP64 accuracy gate at its
+# smallest bond dimension.  Each solve runs the oracle's cyclic Jacobi on
+# matrices up to 1024 x 1024, tens of minutes of CPU per solve, so they run
+# as separate processes and are written to their own file.
+DCUT32_CASES = [
+    (f"ising_{bn}_d32_h{h:g}_n40", "ising", b, h, 32, 40, "paper")
+    for (bn, b) in (("bc", exact.BETA_C), ("b0.40", 0.40), ("b0.48", 0.48))
+    for h in (0.0, 1e-3)
+]
+
+
+def _run_case(case):
+    return case[0], run(*case)
+
+
+def dcut32(names=None):
+    """oracle_solves_dcut32.json: the Dcut-32 coupling grid (or the named
+    subset of it), one process per solve."""
+    import multiprocessing as mp
+    cases = [c for c in DCUT32_CASES if not names or c[0] in names]
+    path = os.path.join(HERE, "oracle_solves_dcut32.json")
+    out = json.load(open(path)) if os.path.exists(path) else {}
+    with mp.get_context("spawn").Pool(len(cases)) as pool:
+        for name, rec in pool.imap_unordered(_run_case, cases):
+            print("oracle done:", name, rec["f"], flush=True)
+            out[name] = rec
+            with open(path, "w") as fh:
+                json.dump(dict(sorted(out.items())), fh, indent=1)
+    print("wrote oracle_solves_dcut32.json")
+
+
 def main():
     if "--expectations" in sys.argv:
         expectations()
+        return
+    if "--dcut32" in sys.argv:
+        dcut32([a for a in sys.argv[1:] if not a.startswith("--")])
         return
     expectations()
     out = {}
