@@ -118,6 +118,16 @@ int trg_set_stream(trg_ctx* ctx, void* stream);
  * called before the first allocation (right after trg_create). */
 int trg_set_allocator(trg_ctx* ctx, trg_alloc_fn alloc, trg_free_fn free_fn, void* user);
 
+/* Limit, in ns, of one bounded device wait of the split products: the
+ * epilogue's wait for a finished accumulator chunk (0 = the default, 2 s).
+ * Every other wait keeps its 2 s limit.  When a wait runs out, the kernel
+ * records a timeout, stops issuing, waits (bounded) for its own copies and
+ * tensor-core work in flight, frees its tensor memory and returns; the call
+ * that launched it returns TRG_ETIMEOUT (trg_gemm clears the flag at its
+ * next call).  A limit below the time of one 512-deep chunk of products
+ * (microseconds) makes that path run; it exists for tests of it. */
+int trg_set_wait_limit(trg_ctx* ctx, uint64_t acc_wait_ns);
+
 /* Change the precision mode for later half-steps (see trg_config). */
 int trg_set_precision(trg_ctx* ctx, int precision, int split_slices, int split_from_step);
 
@@ -180,6 +190,44 @@ int trg_coarse_grain(trg_ctx* ctx, int Dcut, int nsteps);
  * (Sec. 2 and Fig. 1 for the trace, Sec. 3.2 for f = -T ln Z).
  */
 int trg_free_energy(trg_ctx* ctx, double* f_out, double* lnz_per_site);
+
+/* ------------------------------------------- one half-step over ranks */
+/*
+ * A half-step whose contraction is split over several processes (one GPU
+ * each).  The paper runs its contractions on one or two GPUs and reports the
+ * two-GPU speed-up (Sec. 3.1, Sec. 4) without the partition; here the
+ * contraction of Sec. 2 (Tx[i,j,k,l] = sum U[a,b,i] t[b,j,d,c] t[a,c,e,l]
+ * U[e,d,k]) is split over its free index j, the up leg of the upper tensor,
+ * whose slices are independent.  Every rank holds the same tensor and runs
+ * the environment and the isometry itself (same inputs and kernels, so the
+ * same U on every rank), computes the output rows j in [j_begin, j_end), and
+ * the caller exchanges the slabs (an all-gather) before trg_shard_finish.
+ * For a y half-step the formulas see the rotated tensor (as in
+ * trg_coarse_grain), so j is then its left leg.
+ *
+ * trg_shard_extent: *nj_out = the extent of j for the next half-step (Dy for
+ *   an x step, Dx for a y step).
+ * trg_shard_begin: environment, isometry (*dn_out = Dn), and the output rows
+ *   j_begin <= j < j_end written to slab_dev (device, caller-owned, capacity
+ *   slab_cap doubles >= (j_end - j_begin) * Dn * Dn * nj) as
+ *   S[jj][i][k][l] = O[i, j_begin + jj, k, l], O of shape (Dn, nj, Dn, nj).
+ *   An empty range (j_begin == j_end) only runs the first two parts.  Size
+ *   the slab for Dn <= min(Dx^2, Dcut) (Dx the extent of the blocked legs);
+ *   a slab that proves too small gives TRG_EINVAL.  TRG_ESTATE before
+ *   init or while a split half-step is open; TRG_ENOTSUP with an impure
+ *   tensor.
+ * trg_shard_finish: gathered_dev (device) holds G[j][i][k][l] = O[i,j,k,l]
+ *   for j < nj in rows of Dn * Dn * nj doubles (j_rows >= nj rows; rows past
+ *   nj are ignored padding): the slabs of all ranks in j order.  It places O
+ *   as the coarse tensor, normalises it and closes the half-step exactly as
+ *   trg_coarse_grain would; the result is identical to an unsplit half-step.
+ * Between the two calls the context's tensor must not change (no other call
+ * that advances or resets the solve).
+ */
+int trg_shard_extent(trg_ctx* ctx, int* nj_out);
+int trg_shard_begin(trg_ctx* ctx, int Dcut, int j_begin, int j_end, double* slab_dev, size_t slab_cap,
+                    int* dn_out);
+int trg_shard_finish(trg_ctx* ctx, const double* gathered_dev, int j_rows);
 
 /* ------------------------------------------------------- cubic lattice */
 /*

@@ -85,6 +85,7 @@ SIGNATURES = {
     "trg_set_stream": (c_int, [c_void_p, c_void_p]),
     "trg_set_allocator": (c_int, [c_void_p, ALLOC_FN, FREE_FN, c_void_p]),
     "trg_set_precision": (c_int, [c_void_p, c_int, c_int, c_int]),
+    "trg_set_wait_limit": (c_int, [c_void_p, c_uint64]),
     "trg_init_tensor": (c_int, [c_void_p, c_int, c_double, c_double, c_int]),
     "trg_init_tensor_raw": (c_int, [c_void_p, P_double, c_int, c_int, c_double]),
     "trg_init_impure": (c_int, [c_void_p]),
@@ -92,6 +93,9 @@ SIGNATURES = {
     "trg_expectation": (c_int, [c_void_p, P_double]),
     "trg_coarse_grain": (c_int, [c_void_p, c_int, c_int]),
     "trg_free_energy": (c_int, [c_void_p, P_double, P_double]),
+    "trg_shard_extent": (c_int, [c_void_p, P_int]),
+    "trg_shard_begin": (c_int, [c_void_p, c_int, c_int, c_int, c_void_p, c_size_t, P_int]),
+    "trg_shard_finish": (c_int, [c_void_p, c_void_p, c_int]),
     "trg_solve3d": (c_int, [c_void_p, c_int, c_double, c_double, c_int, c_int, P_double, P_double]),
     "trg_get_spectrum": (c_int, [c_void_p, c_int, P_double, c_int, P_int]),
     "trg_get_state": (c_int, [c_void_p, P_int, P_int, P_int, P_double]),

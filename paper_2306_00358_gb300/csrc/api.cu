@@ -112,83 +112,104 @@ static View4 contiguous_view(double* p, int64_t n0, int64_t n1, int64_t n2, int6
     return v;
 }
 
-// One directional blocking.  Step k (1-based): odd = x, even = y.
-static void half_step(Ctx& ctx, int dcut) {
-    const int k = ctx.steps + 1;
-    const bool xdir = (k % 2) == 1;
+// The part of a half-step before its contraction: orientation, environment,
+// isometry.  Step k (1-based): odd = x, even = y.
+static HalfPlan half_step_prepare(Ctx& ctx, int dcut) {
+    HalfPlan p;
+    p.k = ctx.steps + 1;
+    p.xdir = (p.k % 2) == 1;
+    p.precision = precision_for_step(ctx, p.k);
     const int64_t Dx = ctx.Dx, Dy = ctx.Dy;
-    const int precision = precision_for_step(ctx, k);
     View4 t = contiguous_view(ctx.T.as<double>(), Dx, Dy, Dx, Dy);
-    View4 r = t;   // the tensor the x formulas see
-    if (!xdir) {
+    p.r = t;
+    if (!p.xdir) {
         // R = permute(T, (1, 2, 3, 0)): R[p0,p1,p2,p3] = T[p3,p0,p1,p2]
-        r.n[0] = t.n[1]; r.n[1] = t.n[2]; r.n[2] = t.n[3]; r.n[3] = t.n[0];
-        r.s[0] = t.s[1]; r.s[1] = t.s[2]; r.s[2] = t.s[3]; r.s[3] = t.s[0];
+        p.r.n[0] = t.n[1]; p.r.n[1] = t.n[2]; p.r.n[2] = t.n[3]; p.r.n[3] = t.n[0];
+        p.r.s[0] = t.s[1]; p.r.s[1] = t.s[2]; p.r.s[2] = t.s[3]; p.r.s[3] = t.s[0];
     }
-    const int64_t rx = r.n[0], ry = r.n[1];
+    const int64_t rx = p.r.n[0];
     const int64_t n = rx * rx;
     const int64_t dn_max = std::min<int64_t>(n, dcut);
 
     ctx.ensure(ctx.M, (size_t)(n * n) * sizeof(double));
     ctx.ensure(ctx.U, (size_t)(n * dn_max) * sizeof(double));
     ctx.phase = TRG_PHASE_ENV;
-    environment(ctx, r, ctx.M.as<double>(), precision);
+    environment(ctx, p.r, ctx.M.as<double>(), p.precision);
 
-    std::vector<double> lam;
-    int64_t dn = dn_max;
+    p.dn = dn_max;
     ctx.phase = TRG_PHASE_EIG;
     {
         const int tok = ctx.region_begin(TRG_PHASE_EIG);
         if (dn_max == n) {
             launch_identity(ctx, ctx.U.as<double>(), n);
         } else {
-            dn = isometry(ctx, ctx.M.as<double>(), n, dcut, ctx.U.as<double>(), lam, k, precision);
+            p.dn = isometry(ctx, ctx.M.as<double>(), n, dcut, ctx.U.as<double>(), p.lam, p.k, p.precision);
         }
         ctx.region_end(tok, 0.0, 0.0);
     }
+    return p;
+}
 
-    // output O (dn, ry, dn, ry) of the x formulas, written in place of the
-    // coarse tensor (Dx', Dy', Dx', Dy')
-    const int64_t newDx = xdir ? dn : Dx, newDy = xdir ? Dy : dn;
-    const int64_t n_out = newDx * newDy * newDx * newDy;
-    auto out_view = [&](double* base) {
-        if (xdir) return contiguous_view(base, dn, Dy, dn, Dy);
-        // Txy = permute(O, (3, 0, 1, 2)) has shape (ry, dn, ry, dn) = (Dx, dn, Dx, dn)
-        View4 txy = contiguous_view(base, Dx, dn, Dx, dn), o;
-        o.p = txy.p;
-        o.n[0] = dn; o.n[1] = ry; o.n[2] = dn; o.n[3] = ry;
-        o.s[0] = txy.s[1]; o.s[1] = txy.s[2]; o.s[2] = txy.s[3]; o.s[3] = txy.s[0];
-        return o;
-    };
-    ctx.ensure(ctx.Tnext, (size_t)n_out * sizeof(double));
-    contract(ctx, r, r, ctx.U.as<double>(), dn, out_view(ctx.Tnext.as<double>()), precision);
-    if (ctx.have_impure) {
-        // the impurity in the upper and in the lower tensor of the pair, same
-        // isometry (from the pure environment), then the mean of the two
-        View4 ri = contiguous_view(ctx.Timp.as<double>(), Dx, Dy, Dx, Dy);
-        ri.n[0] = r.n[0]; ri.n[1] = r.n[1]; ri.n[2] = r.n[2]; ri.n[3] = r.n[3];
-        ri.s[0] = r.s[0]; ri.s[1] = r.s[1]; ri.s[2] = r.s[2]; ri.s[3] = r.s[3];
-        ctx.ensure(ctx.Timp_next, (size_t)n_out * sizeof(double));
-        ctx.ensure(ctx.Timp_tmp, (size_t)n_out * sizeof(double));
-        contract(ctx, ri, r, ctx.U.as<double>(), dn, out_view(ctx.Timp_next.as<double>()), precision);
-        contract(ctx, r, ri, ctx.U.as<double>(), dn, out_view(ctx.Timp_tmp.as<double>()), precision);
-        launch_mean2(ctx, ctx.Timp_next.as<double>(), ctx.Timp_tmp.as<double>(), n_out);
-    }
+// Output O (dn, ry, dn, ry) of the x formulas, written in place of the coarse
+// tensor (Dx', Dy', Dx', Dy') at `base`.
+static View4 half_step_out_view(const Ctx& ctx, const HalfPlan& p, double* base) {
+    const int64_t dn = p.dn, ry = p.r.n[1];
+    if (p.xdir) return contiguous_view(base, dn, ctx.Dy, dn, ctx.Dy);
+    // Txy = permute(O, (3, 0, 1, 2)) has shape (ry, dn, ry, dn) = (Dx, dn, Dx, dn)
+    View4 txy = contiguous_view(base, ctx.Dx, dn, ctx.Dx, dn), o;
+    o.p = txy.p;
+    o.n[0] = dn; o.n[1] = ry; o.n[2] = dn; o.n[3] = ry;
+    o.s[0] = txy.s[1]; o.s[1] = txy.s[2]; o.s[2] = txy.s[3]; o.s[3] = txy.s[0];
+    return o;
+}
+
+static int64_t half_step_out_elems(const Ctx& ctx, const HalfPlan& p) {
+    const int64_t newDx = p.xdir ? p.dn : ctx.Dx, newDy = p.xdir ? ctx.Dy : p.dn;
+    return newDx * newDy * newDx * newDy;
+}
+
+// Normalise the coarse tensor in Tnext (and the impure one) and make it the
+// current tensor.
+static void half_step_finish(Ctx& ctx, HalfPlan& p) {
+    const int64_t n_out = half_step_out_elems(ctx, p);
     {
         const int tok = ctx.region_begin(TRG_PHASE_NORM);
-        launch_normalise(ctx, ctx.Tnext.as<double>(), n_out, k, false);
+        launch_normalise(ctx, ctx.Tnext.as<double>(), n_out, p.k, false);
         // the impure tensor is divided by the same n_k
         if (ctx.have_impure) launch_scale_by_last_norm(ctx, ctx.Timp_next.as<double>(), n_out);
         ctx.region_end(tok, 0.0, 0.0);
     }
     const int st = read_status(ctx);
-    if (st & ST_BAD_NORM) fail(TRG_ENUMERIC, "non-positive or non-finite norm at half-step " + std::to_string(k));
+    if (st & ST_BAD_NORM) fail(TRG_ENUMERIC, "non-positive or non-finite norm at half-step " + std::to_string(p.k));
     std::swap(ctx.T, ctx.Tnext);
     if (ctx.have_impure) std::swap(ctx.Timp, ctx.Timp_next);
-    ctx.Dx = (int)newDx;
-    ctx.Dy = (int)newDy;
-    ctx.steps = k;
-    ctx.spectra.push_back(lam);
+    ctx.Dx = (int)(p.xdir ? p.dn : ctx.Dx);
+    ctx.Dy = (int)(p.xdir ? ctx.Dy : p.dn);
+    ctx.steps = p.k;
+    ctx.spectra.push_back(std::move(p.lam));
+}
+
+// One directional blocking.
+static void half_step(Ctx& ctx, int dcut) {
+    HalfPlan p = half_step_prepare(ctx, dcut);
+    const int64_t n_out = half_step_out_elems(ctx, p);
+    ctx.ensure(ctx.Tnext, (size_t)n_out * sizeof(double));
+    contract(ctx, p.r, p.r, ctx.U.as<double>(), p.dn, half_step_out_view(ctx, p, ctx.Tnext.as<double>()),
+             p.precision);
+    if (ctx.have_impure) {
+        // the impurity in the upper and in the lower tensor of the pair, same
+        // isometry (from the pure environment), then the mean of the two
+        View4 ri = contiguous_view(ctx.Timp.as<double>(), ctx.Dx, ctx.Dy, ctx.Dx, ctx.Dy);
+        for (int q = 0; q < 4; ++q) { ri.n[q] = p.r.n[q]; ri.s[q] = p.r.s[q]; }
+        ctx.ensure(ctx.Timp_next, (size_t)n_out * sizeof(double));
+        ctx.ensure(ctx.Timp_tmp, (size_t)n_out * sizeof(double));
+        contract(ctx, ri, p.r, ctx.U.as<double>(), p.dn, half_step_out_view(ctx, p, ctx.Timp_next.as<double>()),
+                 p.precision);
+        contract(ctx, p.r, ri, ctx.U.as<double>(), p.dn, half_step_out_view(ctx, p, ctx.Timp_tmp.as<double>()),
+                 p.precision);
+        launch_mean2(ctx, ctx.Timp_next.as<double>(), ctx.Timp_tmp.as<double>(), n_out);
+    }
+    half_step_finish(ctx, p);
 }
 
 static void reset_solve(Ctx& ctx) {
@@ -196,6 +217,7 @@ static void reset_solve(Ctx& ctx) {
     ctx.eig_hint[0] = ctx.eig_hint[1] = Ctx::EigHint();
     ctx.have_tensor = false;
     ctx.have_impure = false;
+    ctx.shard_pending = false;
     ctx.model = -1;
     ctx.steps = 0;
     ctx.spectra.clear();
@@ -355,6 +377,12 @@ int trg_set_allocator(trg_ctx* ctx, trg_alloc_fn alloc, trg_free_fn free_fn, voi
     TRG_GUARD_END(ctx)
 }
 
+int trg_set_wait_limit(trg_ctx* ctx, uint64_t acc_wait_ns) {
+    if (!ctx) return TRG_EINVAL;
+    ctx->acc_wait_ns = acc_wait_ns;
+    return TRG_OK;
+}
+
 int trg_set_precision(trg_ctx* ctx, int precision, int split_slices, int split_from_step) {
     if (!ctx) return TRG_EINVAL;
     trg_config c = ctx->cfg;
@@ -477,9 +505,70 @@ int trg_coarse_grain(trg_ctx* ctx, int Dcut, int nsteps) {
     if (!ctx->have_tensor) return bad(ctx, TRG_ESTATE, "coarse_grain before init_tensor");
     if (Dcut < 1 || nsteps < 0) return bad(ctx, TRG_EINVAL, "Dcut >= 1 and nsteps >= 0 required");
     if (ctx->steps + nsteps > 1000) return bad(ctx, TRG_EINVAL, "more than 1000 half-steps");
+    if (ctx->shard_pending) return bad(ctx, TRG_ESTATE, "coarse_grain between trg_shard_begin and trg_shard_finish");
     TRG_GUARD_BEGIN
     TRG_CUDA(cudaSetDevice(ctx->device));
     for (int i = 0; i < nsteps; ++i) trg::half_step(*ctx, Dcut);
+    return TRG_OK;
+    TRG_GUARD_END(ctx)
+}
+
+int trg_shard_extent(trg_ctx* ctx, int* nj_out) {
+    if (!ctx || !nj_out) return TRG_EINVAL;
+    if (!ctx->have_tensor) return bad(ctx, TRG_ESTATE, "shard_extent before init_tensor");
+    *nj_out = ((ctx->steps + 1) % 2 == 1) ? ctx->Dy : ctx->Dx;
+    return TRG_OK;
+}
+
+int trg_shard_begin(trg_ctx* ctx, int Dcut, int j_begin, int j_end, double* slab_dev, size_t slab_cap,
+                    int* dn_out) {
+    if (!ctx) return TRG_EINVAL;
+    if (!ctx->have_tensor) return bad(ctx, TRG_ESTATE, "shard_begin before init_tensor");
+    if (ctx->shard_pending) return bad(ctx, TRG_ESTATE, "shard_begin twice without shard_finish");
+    if (ctx->have_impure) return bad(ctx, TRG_ENOTSUP, "a split half-step does not carry an impure tensor");
+    if (Dcut < 1 || !dn_out || (!slab_dev && j_end > j_begin)) return bad(ctx, TRG_EINVAL, "shard_begin: bad arguments");
+    if (ctx->steps + 1 > 1000) return bad(ctx, TRG_EINVAL, "more than 1000 half-steps");
+    const int nj = ((ctx->steps + 1) % 2 == 1) ? ctx->Dy : ctx->Dx;
+    if (j_begin < 0 || j_begin > j_end || j_end > nj) return bad(ctx, TRG_EINVAL, "shard_begin: j range outside 0..extent");
+    TRG_GUARD_BEGIN
+    TRG_CUDA(cudaSetDevice(ctx->device));
+    trg::HalfPlan p = trg::half_step_prepare(*ctx, Dcut);
+    const int64_t ry = p.r.n[1], dn = p.dn;
+    if ((size_t)(j_end - j_begin) * (size_t)(dn * dn * ry) > slab_cap)
+        return bad(ctx, TRG_EINVAL, "shard_begin: slab capacity below (j_end - j_begin) Dn^2 extent doubles");
+    if (j_end > j_begin) {
+        // the slab S[jj][i][k][l] of the x formulas' output O[i, j_begin + jj, k, l]
+        trg::View4 o;
+        o.p = slab_dev;
+        o.n[0] = dn; o.n[1] = ry; o.n[2] = dn; o.n[3] = ry;
+        o.s[0] = dn * ry; o.s[1] = dn * dn * ry; o.s[2] = ry; o.s[3] = 1;
+        trg::contract(*ctx, p.r, p.r, ctx->U.as<double>(), dn, o, p.precision, j_begin, j_end, j_begin);
+    }
+    ctx->shard = std::move(p);
+    ctx->shard_pending = true;
+    *dn_out = (int)dn;
+    return TRG_OK;
+    TRG_GUARD_END(ctx)
+}
+
+int trg_shard_finish(trg_ctx* ctx, const double* gathered_dev, int j_rows) {
+    if (!ctx) return TRG_EINVAL;
+    if (!ctx->shard_pending) return bad(ctx, TRG_ESTATE, "shard_finish without shard_begin");
+    const int64_t ry = ctx->shard.r.n[1], dn = ctx->shard.dn;
+    if (!gathered_dev || j_rows < ry) return bad(ctx, TRG_EINVAL, "shard_finish: need all j rows of the gathered output");
+    TRG_GUARD_BEGIN
+    TRG_CUDA(cudaSetDevice(ctx->device));
+    ctx->shard_pending = false;
+    trg::HalfPlan p = std::move(ctx->shard);
+    const int64_t n_out = trg::half_step_out_elems(*ctx, p);
+    ctx->ensure(ctx->Tnext, (size_t)n_out * sizeof(double));
+    // gathered G[j][i][k][l] (rows j >= the extent are padding) -> the coarse tensor
+    trg::View4 g;
+    g.p = const_cast<double*>(gathered_dev);
+    g.n[0] = dn; g.n[1] = ry; g.n[2] = dn; g.n[3] = ry;
+    g.s[0] = dn * ry; g.s[1] = dn * dn * ry; g.s[2] = ry; g.s[3] = 1;
+    trg::launch_copy_strided(*ctx, g, trg::half_step_out_view(*ctx, p, ctx->Tnext.as<double>()));
+    trg::half_step_finish(*ctx, p);
     return TRG_OK;
     TRG_GUARD_END(ctx)
 }
@@ -661,6 +750,8 @@ int trg_gemm(trg_ctx* ctx, int M, int N, int K, const double* A, int lda, const 
     g.B.base = B; g.B.off_r = ctx->table({{K, ldb}}); g.B.off_c = ctx->table({{N, 1}}); g.B.c_fast = true;
     g.C = C; g.c_m = ctx->table({{M, ldc}}); g.c_n = ctx->table({{N, 1}}); g.beta = 0.0;
     ctx->phase = TRG_PHASE_X2;
+    // a status left by an earlier call is not this product's
+    TRG_CUDA(cudaMemsetAsync(ctx->status.p, 0, sizeof(int), ctx->stream));
     trg::gemm(*ctx, g, ctx->cfg.precision);
     TRG_CUDA(cudaStreamSynchronize(ctx->stream));
     if (trg::read_status(*ctx) & trg::ST_TIMEOUT) return bad(ctx, TRG_ETIMEOUT, "gemm: device wait timed out");

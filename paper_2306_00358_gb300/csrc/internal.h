@@ -56,6 +56,18 @@ struct View6 {
     int64_t s[6];
 };
 
+// A half-step between its isometry and its contraction: step k (odd = x,
+// even = y), the tensor the x formulas see (T itself, or its rotation for a
+// y step), the kept dimension and eigenvalues.
+struct HalfPlan {
+    int k = 0;
+    bool xdir = true;
+    int precision = 0;
+    View4 r{};
+    int64_t dn = 0;
+    std::vector<double> lam;   // empty when U = I
+};
+
 struct Ctx {
     int device = 0;
     int sm_count = 0;
@@ -66,6 +78,9 @@ struct Ctx {
     void* alloc_user = nullptr;
     std::string last_error;
     uint64_t launches = 0;
+    // split products: limit of the epilogue's wait for a finished accumulator
+    // chunk in ns (0 = the kernel's default of 2 s); see trg_set_wait_limit
+    unsigned long long acc_wait_ns = 0;
 
     // ---- solve state
     bool have_tensor = false;
@@ -73,6 +88,9 @@ struct Ctx {
     int steps = 0;
     double beta = 0.0;
     Buf T, Tnext;          // current / next site tensor
+    // a half-step split over ranks (trg_shard_begin .. trg_shard_finish)
+    bool shard_pending = false;
+    HalfPlan shard;
     // impure tensor (an observable inserted at one site), blocked alongside T
     bool have_impure = false;
     int model = -1, d0 = 0;    // model of the last trg_init_tensor (-1 after a raw init)
@@ -207,8 +225,11 @@ int slices_now(const Ctx& ctx);
 void environment(Ctx& ctx, const View4& t, double* M, int precision);
 // Tx = U . top . bottom . U (the upper tensor of the blocked pair is `top`,
 // the lower one `bottom`; both the same tensor for the pure half-step).
+// Only the output rows j in [j_begin, j_end) are computed (j_end < 0: all);
+// `out` starts at j = j_out0 (its element (i, j, k, l) is at
+// (j - j_out0) s[1] + ...), so a slab of j can be written on its own.
 void contract(Ctx& ctx, const View4& top, const View4& bottom, const double* U, int64_t Dn, const View4& out,
-              int precision);
+              int precision, int64_t j_begin = 0, int64_t j_end = -1, int64_t j_out0 = 0);
 // Returns Dn actually kept; lam (host) gets the kept eigenvalues.
 int isometry(Ctx& ctx, const double* M, int64_t n, int dcut, double* U, std::vector<double>& lam,
              int step, int precision);

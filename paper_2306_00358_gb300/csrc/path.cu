@@ -138,7 +138,7 @@ void environment(Ctx& ctx, const View4& t, double* M, int precision) {
 // consumer then skips the exponent pass over the D^5 intermediate) or, when
 // the bond dimensions tile (32, 64, 128), writes the consumer's slices.
 void contract(Ctx& ctx, const View4& top, const View4& bottom, const double* U, int64_t Dn, const View4& out,
-              int precision) {
+              int precision, int64_t j_begin, int64_t j_end, int64_t j_out0) {
     const View4& t = top;
     if (bottom.n[0] != top.n[0] || bottom.n[1] != top.n[1] || bottom.n[2] != top.n[2] || bottom.n[3] != top.n[3])
         fail(TRG_EINVAL, "contract: the two tensors of a pair differ in shape");
@@ -148,6 +148,9 @@ void contract(Ctx& ctx, const View4& top, const View4& bottom, const double* U, 
     const int64_t* o = out.s;
     const int64_t DD = Dx * Dy;
     const bool split = precision == TRG_SPLIT_BF16;
+    if (j_end < 0) j_end = Dy;
+    if (j_begin < 0 || j_begin > j_end || j_end > Dy || j_out0 > j_begin)
+        fail(TRG_EINVAL, "contract: bad j range");
     // Fused hand-over (split mode): when a consumer row of the next product is
     // Dx x Dx elements of one 128 x 128 output tile, the producer writes the
     // next product's A slices directly (bit-identical to slicing its FP64
@@ -164,7 +167,7 @@ void contract(Ctx& ctx, const View4& top, const View4& bottom, const double* U, 
     // bytes per j of each intermediate: FP64, or S BF16 slices (+ padding rows)
     const size_t elem = (fuse || fuse1) ? (size_t)std::max(8, 2 * S) : 8;
     const size_t per_j = (size_t)(2 * Dn * Dx * DD) * elem;
-    int64_t jb = std::max<int64_t>(1, std::min<int64_t>(Dy, (int64_t)(ws_cap / per_j)));
+    int64_t jb = std::max<int64_t>(1, std::min<int64_t>(std::max<int64_t>(1, j_end - j_begin), (int64_t)(ws_cap / per_j)));
     const int64_t rows2 = jb * Dn * Dx, rows3 = jb * Dn * Dy;   // A rows of the two consumers
     size_t r1 = (size_t)(rows2 * DD) * 8, r2 = (size_t)(rows3 * Dx * Dx) * 8;
     if (fuse1) r1 = std::max(r1, (size_t)S * split_rows_padded(ctx, rows2) * split_k_padded(DD) * 2);
@@ -181,8 +184,8 @@ void contract(Ctx& ctx, const View4& top, const View4& bottom, const double* U, 
         ef3 = ef2 + rows2;
     }
 
-    for (int64_t j0 = 0; j0 < Dy; j0 += jb) {
-        const int64_t jn = std::min(jb, Dy - j0);
+    for (int64_t j0 = j_begin; j0 < j_end; j0 += jb) {
+        const int64_t jn = std::min(jb, j_end - j0);
         const int64_t M2 = jn * Dn * Dx, M3 = jn * Dn * Dy;       // rows of this block's X2 / O products
         {   // X1[(jj,i,d),(c,a)] = sum_b U[a,b,i] t[b,j0+jj,d,c]: rows (i,a), a fastest,
             // so a warp's lanes hold adjacent a (adjacent in X1, one consumer row)
@@ -268,7 +271,7 @@ void contract(Ctx& ctx, const View4& top, const View4& bottom, const double* U, 
             g.M = M3; g.N = Dn; g.K = Dx * Dx;
             g.A = gather(ctx, X2, {{jb * Dn * Dy, Dx * Dx}}, {{Dx * Dx, 1}});
             g.B = gather(ctx, U, {{Dx, Dx * Dn}, {Dx, Dn}}, {{Dn, 1}});
-            g.C = out.p + j0 * o[1];
+            g.C = out.p + (j0 - j_out0) * o[1];
             g.c_m = ctx.table({{jb, o[1]}, {Dn, o[0]}, {Dy, o[3]}});
             g.c_n = ctx.table({{Dn, o[2]}});
             if (fuse) {

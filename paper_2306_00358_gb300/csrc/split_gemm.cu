@@ -136,12 +136,12 @@ __device__ __forceinline__ bool mbar_try_suspend(uint64_t* bar, uint32_t parity,
 // Bounded wait; returns false (and flags the status word) on expiry or when
 // another role of the CTA has already given up.
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag,
-                                          int* status) {
+                                          int* status, unsigned long long limit_ns = WAIT_NS) {
     if (mbar_try(bar, parity)) return true;
     const unsigned long long t0 = global_ns();
     while (!mbar_try_suspend(bar, parity, 2000u)) {
         if (*abort_flag) return false;
-        if (global_ns() - t0 > WAIT_NS) {
+        if (global_ns() - t0 > limit_ns) {
             *abort_flag = 1;
             atomicOr(status, ST_TIMEOUT);
             return false;
@@ -363,6 +363,9 @@ struct MmaArgs {
     int v_exact53;             // fused: every V is below 2^53 in magnitude (K <= 8192)
     int c_rows_fast;           // C's rows are adjacent: store without staging ...
     int64_t c_col_stride;      // ... with c_n[n + j] = c_n[n] + j c_col_stride in a 32-column group
+    // limit of the epilogue's wait for a finished accumulator chunk (the
+    // other waits keep WAIT_NS); a short one lets tests reach the timeout path
+    unsigned long long acc_wait_ns;
 };
 
 // Tile order: column blocks in groups of group_n; inside a group the tiles run
@@ -709,7 +712,7 @@ k_split_mma(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
             for (int c = 0; c < nchunks && ok; ++c) {
                 // one lane waits, the warp follows (the TMEM loads are warp-collective)
                 int w_ok = 1;
-                if (lane == 0) w_ok = mbar_wait(acc_full, chunk_no & 1, abort_flag, g.status) ? 1 : 0;
+                if (lane == 0) w_ok = mbar_wait(acc_full, chunk_no & 1, abort_flag, g.status, g.acc_wait_ns) ? 1 : 0;
                 ok = __shfl_sync(0xffffffffu, w_ok, 0) != 0;
                 if (!ok) break;
                 tc_fence_after();
@@ -1335,6 +1338,7 @@ void gemm_split(Ctx& ctx, const GemmDesc& d) {
     a.M = M; a.N = N; a.Kp = Kp; a.Mp = Mp; a.Np = Np; a.S = S;
     a.ea = ea; a.eb = eb; a.C = d.C; a.c_m = d.c_m; a.c_n = d.c_n;
     a.status = ctx.status.as<int>();
+    a.acc_wait_ns = ctx.acc_wait_ns ? ctx.acc_wait_ns : WAIT_NS;
     a.cons_ef = d.cons_ef; a.cons_m = d.cons_m; a.cons_n = d.cons_n;
     a.cs_out = d.cs_out; a.cs_plane = d.cs_mp * d.cs_kp; a.cs_kp = d.cs_kp; a.cs_e = d.cs_e;
     a.ck_m = d.ck_m; a.ck_n = d.ck_n; a.rows_per_crow = d.rows_per_crow; a.cols_per_crow = d.cols_per_crow;
@@ -1504,6 +1508,7 @@ extern "C" int trg_gemm_noalloc(int M, int N, int K, const double* A, int lda, c
         a.cs_out = nullptr; a.cs_plane = 0; a.cs_kp = 0; a.cs_e = nullptr; a.ck_m = nullptr; a.ck_n = nullptr;
         a.rows_per_crow = a.cols_per_crow = 0;
         a.ck_stride = 0; a.c_rows_fast = 0; a.c_col_stride = 0; a.v_exact53 = 0;
+        a.acc_wait_ns = WAIT_NS;
         const int tiles = ((M + BM - 1) / BM) * ((N + BN - 1) / BN);
         const int grid = std::max(1, std::min(tiles, sms));
         a.group_n = choose_group_n((M + BM - 1) / BM, (N + BN - 1) / BN, grid, Kp, S);

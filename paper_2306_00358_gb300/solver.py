@@ -107,6 +107,10 @@ class Solver:
         raw = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream or 0)
         self._check(self._lib.trg_set_stream(self._h, ctypes.c_void_p(raw)), "trg_set_stream")
 
+    def set_wait_limit(self, acc_wait_ns: int = 0):
+        """Limit of the split products' accumulator wait (0 = 2 s); see trg_set_wait_limit."""
+        self._check(self._lib.trg_set_wait_limit(self._h, int(acc_wait_ns)), "trg_set_wait_limit")
+
     def set_precision(self, precision, split_slices: int = 4, split_from_step: int = 0):
         p = _PREC[precision] if isinstance(precision, str) else int(precision)
         self._check(self._lib.trg_set_precision(self._h, p, split_slices, split_from_step), "trg_set_precision")
@@ -149,6 +153,27 @@ class Solver:
         lnz = ctypes.c_double()
         self._check(self._lib.trg_free_energy(self._h, ctypes.byref(f), ctypes.byref(lnz)), "trg_free_energy")
         return f.value, lnz.value
+
+    # -- one half-step split over ranks (the caller exchanges the slabs)
+    def shard_extent(self) -> int:
+        nj = ctypes.c_int()
+        self._check(self._lib.trg_shard_extent(self._h, ctypes.byref(nj)), "trg_shard_extent")
+        return nj.value
+
+    def shard_begin(self, dcut: int, j_begin: int, j_end: int, slab) -> int:
+        """Environment, isometry and the output rows j_begin <= j < j_end into
+        `slab` (CUDA float64, at least (j_end - j_begin) Dn^2 nj elements);
+        returns Dn."""
+        _require(slab, 1)
+        dn = ctypes.c_int()
+        self._check(self._lib.trg_shard_begin(self._h, int(dcut), int(j_begin), int(j_end), slab.data_ptr(),
+                                              slab.numel(), ctypes.byref(dn)), "trg_shard_begin")
+        return dn.value
+
+    def shard_finish(self, gathered, j_rows: int):
+        """Place the gathered output (rows j of Dn^2 nj elements) and close the half-step."""
+        _require(gathered, 1)
+        self._check(self._lib.trg_shard_finish(self._h, gathered.data_ptr(), int(j_rows)), "trg_shard_finish")
 
     def solve3d(self, beta: float, h: float, dcut: int, nsteps: int, model: str = "ising"):
         """A whole cubic-lattice solve (steps z, x, y, ...): returns (f, ln Z / V)."""
