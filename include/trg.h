@@ -69,7 +69,9 @@ typedef struct trg_config {
     int precision;           /* trg_precision (default TRG_FP64) */
     int split_slices;        /* BF16 slices per operand in TRG_SPLIT_BF16, 2..5 (default 4);
                                 the contraction products use it (see env_slices) */
-    int split_from_step;     /* half-steps with index < this run in FP64 (default 0) */
+    int split_from_step;     /* in TRG_SPLIT_BF16 the half-steps k <= split_from_step run in FP64
+                                (default 2: steps 1 and 2 hold bond dimensions 2 and 4, cost
+                                nothing, and their norms weigh 1/2 and 1/4 in ln Z / V) */
     int trunc;               /* trg_trunc (default TRG_TRUNC_PAPER) */
     double gap_tol;          /* multiplet gap, relative to lambda_1 (default 1e-6; in
                                 TRG_SPLIT_BF16 at least 2^-(8*S-12), S = the env slices) */

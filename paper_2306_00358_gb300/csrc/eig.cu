@@ -654,11 +654,17 @@ int isometry(Ctx& ctx, const double* M, int64_t n, int dcut, double* U, std::vec
         gram(ctx, Q, Y, n, m, G, TRG_FP64);
         TRG_CUDA(cudaMemsetAsync(sweeps, 0, 2 * sizeof(int), ctx.stream));
         const int full = (rr_done > 0 || m == n) ? 1 : 0;
-        // FP64 rotations stop at |h_pq| <= 1e-13 sqrt(h_pp h_qq): the FP32 sweeps
-        // leave ~1e-7, one quadratically convergent FP64 sweep ~1e-14, so the
-        // next sweep only confirms (the eigenvalues are then exact to ~1e-26
-        // relative, the vectors of pairs with a relative gap g to ~1e-13 / g)
-        k_jacobi<<<1, 512, jac_smem, ctx.stream>>>(G, m, 1e-13, 60, theta, W, L, status, sweeps, full);
+        // FP64 rotations stop at |h_pq| <= jtol sqrt(h_pp h_qq).  An unrotated
+        // pair leaves at most m jtol theta_1 in a Ritz residual, so jtol =
+        // 1e-3 tol keeps that far below the tolerance; with FP64 products
+        // (tol 1e-12) it is 1e-13: the FP32 sweeps leave ~1e-7, one
+        // quadratically convergent FP64 sweep ~1e-14, and the next sweep only
+        // confirms (eigenvalues exact to ~1e-26 relative, the vectors of pairs
+        // with a relative gap g to ~1e-13 / g).  With split products (tol
+        // 2^-(8S-10)) the first FP64 sweep already reaches jtol, which saves a
+        // whole sweep of rotations.
+        const double jtol = std::max(1e-13, 1e-3 * tol);
+        k_jacobi<<<1, 512, jac_smem, ctx.stream>>>(G, m, jtol, 60, theta, W, L, status, sweeps, full);
         TRG_LAUNCHED(ctx);
         times_small(ctx, Y, W, n, m, Z);
         times_small(ctx, Q, W, n, m, QW);
