@@ -45,9 +45,12 @@ def parse():
     ap.add_argument("--no-accuracy", action="store_true",
                     help="skip the headline accuracy leg (split and FP64 solves of the Dcut-64 beta_c workload)")
     ap.add_argument("--no-calibration", action="store_true", help="skip the in-run calibration products")
+    ap.add_argument("--workspace-bytes", type=int, default=0,
+                    help="bound of the contraction workspace (0 = the library default, 4 GiB: 16 values of j "
+                         "per D^7 launch at Dcut 64)")
     ap.add_argument("--fused-slices", type=int, default=1, choices=[0, 1, 2],
                     help="slice hand-over between contraction products: none (0), D^7 -> last (1), all (2)")
-    ap.add_argument("--mma-pairs", type=int, default=0, choices=[0, 1],
+    ap.add_argument("--mma-pairs", type=int, default=1, choices=[0, 1],
                     help="split products on CTA pairs (1) or one CTA per tile (0)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -373,6 +376,8 @@ def run_native(args):
 
     stream = torch.cuda.current_stream()
     extra = {"env_slices": args.env_slices} if args.env_slices else {}
+    if args.workspace_bytes:
+        extra["workspace_bytes"] = args.workspace_bytes
     s = Solver(local, stream=stream, precision=precision, split_slices=args.slices, mma_pairs=args.mma_pairs,
                fused_slices=args.fused_slices, **extra)
     beta = replica_beta(rank)
@@ -429,7 +434,8 @@ def run_native(args):
         alg = x2_algorithmic_bytes(args.slices)
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": traffic,
-                "kernel": "k_split_mma<%d,1,EPI_FUSED> (X2 = X1.t, the D^7 product)" % args.slices,
+                "kernel": "k_split_mma<%d,%d,EPI_FUSED> (X2 = X1.t, the D^7 product%s)" % (
+                    args.slices, 2 if args.mma_pairs else 1, ", CTA pairs" if args.mma_pairs else ""),
                 "launches_per_step": mx["calls"] / steps, "ms_per_launch": t_launch * 1e3,
                 "fp64_equiv_tflops": mx["flops"] / calls / t_launch / 1e12 if t_launch > 0 else 0.0,
                 "split_roofline_fp64_equiv": peak / products,

@@ -81,10 +81,11 @@ typedef struct trg_config {
     int eig_max_iter;        /* subspace iterations before TRG_ENUMERIC (default 300) */
     uint64_t seed;           /* seed of the start block of the subspace iteration */
     size_t workspace_bytes;  /* bound on the contraction workspace (0 = 4 GiB) */
-    int mma_pairs;           /* TRG_SPLIT_BF16: 1 runs products with more than 128 rows on
-                                CTA pairs (256-row tiles, cta_group::2, each CTA staging
-                                half of B); 0 (default) keeps one CTA per 128 x 128 tile.
-                                Results are identical either way. */
+    int mma_pairs;           /* TRG_SPLIT_BF16: 1 (default) runs products with more than 128
+                                rows on CTA pairs (256-row tiles, cta_group::2: every
+                                tensor-core instruction drives two SMs, each staging half
+                                of B); 0 keeps one CTA per 128 x 128 tile.  Results are
+                                identical either way. */
     int fused_slices;        /* TRG_SPLIT_BF16, bond dimensions 32, 64 or 128: 1 (default)
                                 lets the D^7 contraction product write the last product's
                                 BF16 operand slices directly (no FP64 intermediate, no
@@ -106,8 +107,13 @@ typedef void (*trg_free_fn)(void* ptr, size_t bytes, void* stream, void* user);
 /* Fill *cfg with the defaults listed above. */
 int trg_config_default(trg_config* cfg);
 
-/* Create a context on CUDA device `device`.  cfg may be NULL (defaults).
- * Returns TRG_ENOTSUP if the device is not sm_103 (GB300). */
+/* Create a context on CUDA device `device`: the state of one free-energy
+ * solve of Sec. 2 (the site tensor, its norms and the coarse-graining
+ * settings; the paper keeps the same state in Python variables between the
+ * calls of its coarse-graining listing).  cfg may be NULL (defaults).
+ * *out receives the handle (NULL on failure).  Returns TRG_EINVAL for a bad
+ * device index or config, TRG_ENOTSUP if the device is not sm_103 (GB300),
+ * TRG_ENOMEM / TRG_ECUDA if its two small device buffers cannot be made. */
 int trg_create(trg_ctx** out, int device, const trg_config* cfg);
 
 /* Destroy a context and free all device memory it allocated. NULL is a no-op. */
@@ -130,7 +136,13 @@ int trg_set_allocator(trg_ctx* ctx, trg_alloc_fn alloc, trg_free_fn free_fn, voi
  * (microseconds) makes that path run; it exists for tests of it. */
 int trg_set_wait_limit(trg_ctx* ctx, uint64_t acc_wait_ns);
 
-/* Change the precision mode for later half-steps (see trg_config). */
+/* Change the precision mode for later half-steps (see trg_config).  The
+ * paper does not state the arithmetic of its contractions (PyTorch float64
+ * tensors, Sec. 3 and the appendix); TRG_FP64 is that reading, and
+ * TRG_SPLIT_BF16 with split_slices BF16 slices per operand is this library's
+ * tensor-core form of the same products.  split_from_step keeps the
+ * half-steps k <= split_from_step in FP64.  Invalid values: TRG_EINVAL and
+ * the context keeps its settings. */
 int trg_set_precision(trg_ctx* ctx, int precision, int split_slices, int split_from_step);
 
 /* -------------------------------------------------------- full solve ---- */
@@ -259,9 +271,12 @@ int trg_shard_finish(trg_ctx* ctx, const double* gathered_dev, int j_rows);
 int trg_solve3d(trg_ctx* ctx, int model, double beta, double h, int Dcut, int nsteps, double* f_out,
                 double* lnz_per_site);
 
-/* Kept eigenvalues of M at half-step `step` (1-based), descending, written
- * to out[0..min(cap,n)-1]; *n_out = number kept.  Untruncated steps (U = I)
- * report n_out = 0. */
+/* Kept eigenvalues of M at half-step `step` (1-based): the squared singular
+ * values that the SVD helper of the coarse-graining listing (Sec. 2) ranks
+ * to truncate, M being a Gram matrix.  Descending, written to
+ * out[0..min(cap,n)-1] (host, caller-owned; out may be NULL to query n);
+ * *n_out = number kept.  Untruncated steps (U = I) report n_out = 0.
+ * TRG_EINVAL for a step outside 1..half-steps done. */
 int trg_get_spectrum(trg_ctx* ctx, int step, double* out, int cap, int* n_out);
 
 /* Current solve state: half-steps done, (Dx, Dy), and sum_k 2^-k ln n_k. */

@@ -279,7 +279,7 @@ int trg_config_default(trg_config* cfg) {
     cfg->eig_max_iter = 300;
     cfg->seed = 0x5EEDull;
     cfg->workspace_bytes = 0;
-    cfg->mma_pairs = 0;
+    cfg->mma_pairs = 1;
     cfg->fused_slices = 1;
     cfg->env_slices = 0;
     return TRG_OK;

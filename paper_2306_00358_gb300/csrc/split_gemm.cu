@@ -35,12 +35,15 @@
 // shared-memory cycles that the MMA operand reads need).  Every wait is
 // bounded: on expiry the kernel records ST_TIMEOUT and leaves its loops.
 //
-// A second instance runs each 256 x 128 tile on a CTA pair (cta_group::2):
-// each CTA stages its own 128 rows of A and every other B slice in full (the
-// even CTA B0, B2, ..., the odd one B1, B3, ...), so every instruction is a
-// 256 x 256 x 16 product A_p [B_2b | B_2b+1] that drives both SMs; the even
-// CTA issues for both, and its barriers collect the loads and TMEM drains of
-// the pair (pair_ins_of).  Off by default (mma_pairs).
+// A second instance runs each 256 x 128 tile on a CTA pair (cta_group::2)
+// with the same product table at M = 256: a wide entry A_p [B_b | B_b+1]
+// takes B_b from the even CTA and B_b+1 from the odd one (each CTA stages one
+// slice of every wide pair), a narrow entry A_p B_q takes 64 of B_q's columns
+// from each CTA (half-height tiles).  Every instruction then drives both SMs,
+// so the issuing thread (the even CTA's) needs half the instructions per
+// product, and each SM reads less operand data from shared memory; the even
+// CTA's barriers collect the loads and TMEM drains of the pair.  Enabled by
+// mma_pairs.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
@@ -70,28 +73,44 @@ constexpr int SMEM_LIMIT = 232448;             // opt-in shared memory per block
 constexpr int BAR_BYTES = 512;                 // mbarriers, TMEM address, flags, row maxima
 
 // CG = CTAs per MMA (1, or a pair with cta_group::2).  A CTA stages its own
-// 128 rows of A (all S slices) and 128-row B slice tiles per stage.
-// B tiles a CTA stages per stage: all S (one CTA), or every other slice on a
-// pair (the even CTA B0, B2, ..., the odd one B1, B3, ...; for odd S the last
-// one is past the slice array and TMA fills it with zeros).
-__host__ __device__ constexpr int b_tiles(int S, int CG) { return CG == 1 ? S : (S + 1) / 2; }
-__host__ __device__ constexpr int stage_bytes_for(int S, int CG) { return (S + b_tiles(S, CG)) * TILE_BYTES; }
-__host__ __device__ constexpr int stages_for(int S, int CG) {
-    return CG == 1 ? (S <= 4 ? 3 : 2)
-                   : ((SMEM_LIMIT - 1024 - BAR_BYTES - STAGING_BYTES) / stage_bytes_for(S, CG) > 6
-                          ? 6
-                          : (SMEM_LIMIT - 1024 - BAR_BYTES - STAGING_BYTES) / stage_bytes_for(S, CG));
+// 128 rows of A (all S slices) per stage, and B as follows.  One CTA: all S
+// 128-row B slice tiles.  A pair issues the single-CTA product table (ins_of)
+// with M = 256: a wide entry A_p [B_b | B_b+1] (b even) takes its first 128
+// columns from the even CTA and the other 128 from the odd one, so each CTA
+// holds one slice of every wide pair (the even CTA B0, B2, the odd one B1,
+// B3: pair_wide_tiles); a narrow entry A_p B_q (q even, N = 128) takes 64 of
+// B_q's 128 columns from each CTA, staged as half-height tiles
+// (pair_half_tiles).  Both CTAs' accumulators then receive exactly the
+// single-CTA products of their own rows.
+constexpr int HALF_TILE_BYTES = TILE_BYTES / 2;  // 64 x 32 BF16
+__host__ __device__ constexpr int pair_wide_tiles(int S) { return S >= 4 ? 2 : 1; }
+__host__ __device__ constexpr int pair_half_tiles(int S) { return S == 2 ? 1 : S == 5 ? 3 : 2; }
+__host__ __device__ constexpr int stage_bytes_for(int S, int CG) {
+    return CG == 1 ? 2 * S * TILE_BYTES : (S + pair_wide_tiles(S)) * TILE_BYTES + pair_half_tiles(S) * HALF_TILE_BYTES;
 }
-__host__ __device__ constexpr int smem_bytes_for(int S, int CG) {
+// Only the staged epilogue uses the store staging tile; the other two leave
+// its 32 KB to the operand pipeline, which a pair turns into one more stage.
+__host__ __device__ constexpr int staging_bytes_for(int MODE) { return MODE == 0 ? STAGING_BYTES : 0; }
+__host__ __device__ constexpr int stages_for(int S, int CG, int MODE) {
+    return CG == 1 ? (S <= 4 ? 3 : 2)
+                   : ((SMEM_LIMIT - 1024 - BAR_BYTES - staging_bytes_for(MODE)) / stage_bytes_for(S, CG) > 6
+                          ? 6
+                          : (SMEM_LIMIT - 1024 - BAR_BYTES - staging_bytes_for(MODE)) / stage_bytes_for(S, CG));
+}
+__host__ __device__ constexpr int smem_bytes_for(int S, int CG, int MODE) {
     // at least 120 KB so that a second CTA (and its 512 TMEM columns) never shares the SM
-    return (stages_for(S, CG) * stage_bytes_for(S, CG) + 1024 + BAR_BYTES + STAGING_BYTES) > 120 * 1024
-               ? stages_for(S, CG) * stage_bytes_for(S, CG) + 1024 /*align*/ + BAR_BYTES + STAGING_BYTES
+    return (stages_for(S, CG, MODE) * stage_bytes_for(S, CG) + 1024 + BAR_BYTES + staging_bytes_for(MODE)) > 120 * 1024
+               ? stages_for(S, CG, MODE) * stage_bytes_for(S, CG) + 1024 /*align*/ + BAR_BYTES + staging_bytes_for(MODE)
                : 120 * 1024;
 }
-static_assert(smem_bytes_for(2, 2) <= SMEM_LIMIT && smem_bytes_for(3, 2) <= SMEM_LIMIT &&
-                  smem_bytes_for(4, 2) <= SMEM_LIMIT && smem_bytes_for(5, 2) <= SMEM_LIMIT &&
-                  smem_bytes_for(5, 1) <= SMEM_LIMIT,
-              "split MMA shared memory");
+constexpr bool smem_fits() {
+    for (int S = 2; S <= 5; ++S)
+        for (int CG = 1; CG <= 2; ++CG)
+            for (int MODE = 0; MODE <= 2; ++MODE)
+                if (smem_bytes_for(S, CG, MODE) > SMEM_LIMIT || stages_for(S, CG, MODE) < 2) return false;
+    return true;
+}
+static_assert(smem_fits(), "split MMA shared memory");
 
 // ------------------------------------------------------------ PTX helpers
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -440,55 +459,19 @@ __host__ __device__ constexpr bool ins_cover_ok(int S) {
 }
 static_assert(ins_cover_ok(2) && ins_cover_ok(3) && ins_cover_ok(4) && ins_cover_ok(5), "slice product table");
 
-// The same for a CTA pair.  Entry b is the pair of B slices (2b, 2b+1) (the
-// even CTA holds 2b, the odd one 2b+1), always N = 256 across the pair
-// (each instruction drives both SMs for 128 x 256 x 16), so single products
-// are paired with one more: A1 B3 and A3 B1 (S = 4), A2 B3 and A4 B1 (S = 5)
-// go into R2 at p + q = S, beyond the truncation (more accurate, not less);
-// with S = 2, 3 the epilogue ignores R / R2 as it does for one CTA.
-__host__ __device__ constexpr int pair_ins_count(int S) { return S == 2 ? 2 : S == 3 ? 4 : S == 4 ? 6 : 9; }
-__host__ __device__ constexpr SliceIns pair_ins_of(int S, int t) {
-    return S == 2 ? (t == 0 ? SliceIns{0, 0, 1, 0, 0, 1} : SliceIns{1, 0, 1, 128, 2, 1})
-         : S == 3 ? (t == 0 ? SliceIns{0, 0, 1, 0, 0, 1}
-                   : t == 1 ? SliceIns{2, 0, 1, 256, 1, 1}
-                   : t == 2 ? SliceIns{1, 0, 1, 128, 2, 1}
-                            : SliceIns{0, 1, 1, 256, 2, 2})
-         : S == 4 ? (t == 0 ? SliceIns{0, 0, 1, 0, 0, 1}
-                   : t == 1 ? SliceIns{2, 0, 1, 256, 1, 1}
-                   : t == 2 ? SliceIns{1, 0, 1, 128, 2, 1}
-                   : t == 3 ? SliceIns{0, 1, 1, 256, 2, 2}
-                   : t == 4 ? SliceIns{1, 1, 1, 256, 2, 2}
-                            : SliceIns{3, 0, 1, 256, 2, 2})
-                  : (t == 0 ? SliceIns{0, 0, 1, 0, 0, 1}
-                   : t == 1 ? SliceIns{2, 0, 1, 256, 1, 1}
-                   : t == 2 ? SliceIns{1, 0, 1, 128, 2, 1}
-                   : t == 3 ? SliceIns{0, 1, 1, 256, 2, 2}
-                   : t == 4 ? SliceIns{1, 1, 1, 256, 2, 2}
-                   : t == 5 ? SliceIns{3, 0, 1, 256, 2, 2}
-                   : t == 6 ? SliceIns{2, 1, 1, 256, 2, 2}
-                   : t == 7 ? SliceIns{0, 2, 1, 256, 2, 2}
-                            : SliceIns{4, 0, 1, 256, 2, 2});
-}
-// Every product p + q < S exactly once; extra products only at p + q >= S
-// and never into ACC0 / ACC1 (columns < 256), whose sums must stay exact.
-__host__ __device__ constexpr bool pair_cover_ok(int S) {
-    int seen[6][6] = {};
-    for (int t = 0; t < pair_ins_count(S); ++t) {
-        const SliceIns in = pair_ins_of(S, t);
-        for (int h = 0; h < 2; ++h) {
-            const int p = in.a, q = 2 * in.b + h, col = in.col + 128 * h;
-            if (p >= S || q > S) return false;
-            if (q < S) seen[p][q] += 1;
-            if (p + q >= S && col < 256) return false;
-            if (col >= 512) return false;
-        }
+// A pair issues the same table: every wide entry starts at an even B slice
+// whose pair a CTA stages (b / 2 < pair_wide_tiles), every narrow entry reads
+// an even B slice staged as half tiles (q / 2 < pair_half_tiles).
+__host__ __device__ constexpr bool pair_table_ok(int S) {
+    for (int t = 0; t < ins_count(S); ++t) {
+        const SliceIns in = ins_of(S, t);
+        if (in.b % 2 != 0) return false;
+        if (in.wide && (in.b / 2 >= pair_wide_tiles(S) || in.b + 1 >= S)) return false;
+        if (!in.wide && in.b / 2 >= pair_half_tiles(S)) return false;
     }
-    for (int p = 0; p < S; ++p)
-        for (int q = 0; q < S; ++q)
-            if (p + q < S && seen[p][q] != 1) return false;
     return true;
 }
-static_assert(pair_cover_ok(2) && pair_cover_ok(3) && pair_cover_ok(4) && pair_cover_ok(5), "pair product table");
+static_assert(pair_table_ok(2) && pair_table_ok(3) && pair_table_ok(4) && pair_table_ok(5), "pair staging");
 
 // Epilogue kinds: FP64 results stored through a staging tile (columns
 // adjacent in C), stored directly (rows adjacent in C), or the consumer's
@@ -498,11 +481,12 @@ enum EpiMode { EPI_STAGED = 0, EPI_DIRECT = 1, EPI_FUSED = 2 };
 
 template <int S, int CG, int MODE>
 __global__ void __launch_bounds__(THREADS, 1)
-k_split_mma(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, const MmaArgs g) {
-    constexpr int STAGES = stages_for(S, CG);
+k_split_mma(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+            const __grid_constant__ CUtensorMap tmBh, const MmaArgs g) {
+    constexpr int STAGES = stages_for(S, CG, MODE);
     constexpr int STAGE_BYTES = stage_bytes_for(S, CG);
     constexpr int B_TILE = TILE_BYTES;
-    constexpr int NB = b_tiles(S, CG);            // B slice tiles this CTA stages
+    constexpr int PW = pair_wide_tiles(S), PH = pair_half_tiles(S);   // pair staging (CG = 2)
     constexpr int TILE_M = BM * CG;                // output rows per tile (per CTA pair)
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -579,20 +563,24 @@ k_split_mma(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
                     if (!ok) break;
                     uint8_t* st = smem + stage * STAGE_BYTES;
                     if (rank == 0) mbar_expect_tx(&full[stage], CG * STAGE_BYTES);   // both CTAs' bytes
-                    for (int p = 0; p < S; ++p) {
-                        if constexpr (CG == 1) {
+                    if constexpr (CG == 1) {
+                        for (int p = 0; p < S; ++p) {
                             tma_load_2d(st + p * TILE_BYTES, &tmA, kb * BK, p * g.Mp + arow, &full[stage]);
                             tma_load_2d(st + S * TILE_BYTES + p * B_TILE, &tmB, kb * BK, p * g.Np + brow,
                                         &full[stage]);
-                        } else {
-                            const uint32_t bar = leader_full0 + (uint32_t)(stage * sizeof(uint64_t));
-                            tma_load_2d_pair(st + p * TILE_BYTES, &tmA, kb * BK, p * g.Mp + arow, bar);
-                            if (p < NB) {
-                                // B slice 2p + rank (rows past the array read as zeros)
-                                tma_load_2d_pair(st + S * TILE_BYTES + p * B_TILE, &tmB, kb * BK,
-                                                 (2 * p + (int)rank) * g.Np + brow, bar);
-                            }
                         }
+                    } else {
+                        const uint32_t bar = leader_full0 + (uint32_t)(stage * sizeof(uint64_t));
+                        for (int p = 0; p < S; ++p)
+                            tma_load_2d_pair(st + p * TILE_BYTES, &tmA, kb * BK, p * g.Mp + arow, bar);
+                        // wide pairs: this CTA's slice 2w + rank of the pair (2w, 2w + 1)
+                        for (int w = 0; w < PW; ++w)
+                            tma_load_2d_pair(st + S * TILE_BYTES + w * B_TILE, &tmB, kb * BK,
+                                             (2 * w + (int)rank) * g.Np + brow, bar);
+                        // narrow products: this CTA's 64 columns of slice 2h
+                        for (int h = 0; h < PH; ++h)
+                            tma_load_2d_pair(st + (S + PW) * TILE_BYTES + h * HALF_TILE_BYTES, &tmBh, kb * BK,
+                                             2 * h * g.Np + brow + (int)rank * (BN / 2), bar);
                     }
 #pragma unroll
                     for (int s = 0; s < STAGES; ++s)
@@ -635,18 +623,22 @@ k_split_mma(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
 #pragma unroll
                         for (int kk = 0; kk < BK / 16; ++kk) {
 #pragma unroll
-                            for (int t = 0; t < (CG == 1 ? ins_count(S) : pair_ins_count(S)); ++t) {
-                                const SliceIns in = CG == 1 ? ins_of(S, t) : pair_ins_of(S, t);
+                            for (int t = 0; t < ins_count(S); ++t) {
+                                const SliceIns in = ins_of(S, t);
                                 if (in.group != group) continue;
                                 uint32_t acc = 1u;
                                 if (in.flag == 0) acc = (chunk_start && kk == 0) ? 0u : 1u;
                                 if (in.flag == 1) acc = (kb == 0 && kk == 0) ? 0u : 1u;
                                 const uint64_t da = dbase + (uint64_t)((in.a * TILE_BYTES + kk * 32) >> 4);
-                                const uint64_t db = dbase + (uint64_t)((S * TILE_BYTES + in.b * B_TILE + kk * 32) >> 4);
                                 // one CTA: B_q and B_q+1 are adjacent 128-row tiles, so a wide entry is
-                                // one N = 256 product; a pair: B tile b of the even CTA and the one at
-                                // the same place in the odd CTA, every entry 256 x 256
-                                mma_bf16<CG>(tmem + in.col, da, db, (CG == 2 || in.wide) ? IDESC_N256 : IDESC, acc);
+                                // one N = 256 product.  A pair: a wide entry reads the pair's tile b / 2
+                                // (B_b in the even CTA, B_b+1 in the odd one), a narrow one the half
+                                // tiles of B_b (64 columns in each CTA)
+                                const int boff = CG == 1 ? S * TILE_BYTES + in.b * B_TILE
+                                               : in.wide ? (S + in.b / 2) * TILE_BYTES
+                                                         : (S + PW) * TILE_BYTES + (in.b / 2) * HALF_TILE_BYTES;
+                                const uint64_t db = dbase + (uint64_t)((boff + kk * 32) >> 4);
+                                mma_bf16<CG>(tmem + in.col, da, db, in.wide ? IDESC_N256 : IDESC, acc);
                             }
                         }
                     };
@@ -1163,13 +1155,14 @@ int choose_group_n(int tiles_m, int tiles_n, int grid, int kp, int S) {
 }
 
 template <int S, int CG, int MODE>
-void launch_mma_k(Ctx& ctx, const CUtensorMap& ta, const CUtensorMap& tb, const MmaArgs& a0) {
+void launch_mma_k(Ctx& ctx, const CUtensorMap& ta, const CUtensorMap& tb, const CUtensorMap& tbh,
+                  const MmaArgs& a0) {
     MmaArgs a = a0;
     static std::once_flag once;
     static int max_clusters = 0;
     std::call_once(once, [&ctx] {
         TRG_CUDA(cudaFuncSetAttribute(k_split_mma<S, CG, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      smem_bytes_for(S, CG)));
+                                      smem_bytes_for(S, CG, MODE)));
         if (CG == 2) {
             // pairs that can be resident at once (a persistent grid must not exceed it)
             cudaLaunchConfig_t cfg = {};
@@ -1178,7 +1171,7 @@ void launch_mma_k(Ctx& ctx, const CUtensorMap& ta, const CUtensorMap& tb, const 
             attr[0].val.clusterDim.x = 2; attr[0].val.clusterDim.y = 1; attr[0].val.clusterDim.z = 1;
             cfg.gridDim = dim3((unsigned)(ctx.sm_count & ~1));
             cfg.blockDim = dim3(THREADS);
-            cfg.dynamicSmemBytes = smem_bytes_for(S, CG);
+            cfg.dynamicSmemBytes = smem_bytes_for(S, CG, MODE);
             cfg.attrs = attr;
             cfg.numAttrs = 1;
             TRG_CUDA(cudaOccupancyMaxActiveClusters(&max_clusters, k_split_mma<S, CG, MODE>, &cfg));
@@ -1191,7 +1184,7 @@ void launch_mma_k(Ctx& ctx, const CUtensorMap& ta, const CUtensorMap& tb, const 
     cudaError_t e;
     if (CG == 1) {
         const int grid = ctas;
-        k_split_mma<S, CG, MODE><<<grid, THREADS, smem_bytes_for(S, CG), ctx.stream>>>(ta, tb, a);
+        k_split_mma<S, CG, MODE><<<grid, THREADS, smem_bytes_for(S, CG, MODE), ctx.stream>>>(ta, tb, tbh, a);
         e = cudaGetLastError();
     } else {
         if (max_clusters < 1) fail(TRG_ENOTSUP, "split MMA: no CTA pair fits on this device");
@@ -1202,11 +1195,11 @@ void launch_mma_k(Ctx& ctx, const CUtensorMap& ta, const CUtensorMap& tb, const 
         attr[0].val.clusterDim.x = 2; attr[0].val.clusterDim.y = 1; attr[0].val.clusterDim.z = 1;
         cfg.gridDim = dim3((unsigned)(2 * pairs));
         cfg.blockDim = dim3(THREADS);
-        cfg.dynamicSmemBytes = smem_bytes_for(S, CG);
+        cfg.dynamicSmemBytes = smem_bytes_for(S, CG, MODE);
         cfg.stream = ctx.stream;
         cfg.attrs = attr;
         cfg.numAttrs = 1;
-        e = cudaLaunchKernelEx(&cfg, k_split_mma<S, CG, MODE>, ta, tb, a);
+        e = cudaLaunchKernelEx(&cfg, k_split_mma<S, CG, MODE>, ta, tb, tbh, a);
         if (e == cudaSuccess) e = cudaGetLastError();
     }
     ctx.launches++;
@@ -1215,17 +1208,17 @@ void launch_mma_k(Ctx& ctx, const CUtensorMap& ta, const CUtensorMap& tb, const 
         cudaFuncGetAttributes(&fa, k_split_mma<S, CG, MODE>);
         fail(TRG_ECUDA, std::string("split MMA launch: ") + cudaGetErrorString(e) + " (regs " +
                             std::to_string(fa.numRegs) + ", max threads " + std::to_string(fa.maxThreadsPerBlock) +
-                            ", dyn smem " + std::to_string(smem_bytes_for(S, CG)) + " / " +
+                            ", dyn smem " + std::to_string(smem_bytes_for(S, CG, MODE)) + " / " +
                             std::to_string(fa.maxDynamicSharedSizeBytes) + ", local " +
                             std::to_string(fa.localSizeBytes) + ")");
     }
 }
 
 template <int S, int CG>
-void launch_mma(Ctx& ctx, const CUtensorMap& ta, const CUtensorMap& tb, const MmaArgs& a) {
-    if (a.cs_out) launch_mma_k<S, CG, EPI_FUSED>(ctx, ta, tb, a);
-    else if (a.c_rows_fast) launch_mma_k<S, CG, EPI_DIRECT>(ctx, ta, tb, a);
-    else launch_mma_k<S, CG, EPI_STAGED>(ctx, ta, tb, a);
+void launch_mma(Ctx& ctx, const CUtensorMap& ta, const CUtensorMap& tb, const CUtensorMap& tbh, const MmaArgs& a) {
+    if (a.cs_out) launch_mma_k<S, CG, EPI_FUSED>(ctx, ta, tb, tbh, a);
+    else if (a.c_rows_fast) launch_mma_k<S, CG, EPI_DIRECT>(ctx, ta, tb, tbh, a);
+    else launch_mma_k<S, CG, EPI_STAGED>(ctx, ta, tb, tbh, a);
 }
 
 template <int S>
@@ -1334,6 +1327,8 @@ void gemm_split(Ctx& ctx, const GemmDesc& d) {
     }
     const CUtensorMap ta = make_map(sa, S * Mp, Kp);
     const CUtensorMap tb = make_map(sb, S * Np, Kp);
+    // a pair also reads B as 64-row half tiles (its narrow products)
+    const CUtensorMap tbh = CG == 2 ? make_map(sb, S * Np, Kp, BN / 2) : tb;
     MmaArgs a;
     a.M = M; a.N = N; a.Kp = Kp; a.Mp = Mp; a.Np = Np; a.S = S;
     a.ea = ea; a.eb = eb; a.C = d.C; a.c_m = d.c_m; a.c_n = d.c_n;
@@ -1358,14 +1353,14 @@ void gemm_split(Ctx& ctx, const GemmDesc& d) {
     const int tok = ctx.region_begin(TRG_PHASE_MMA);
     const int tok_x2 = ctx.phase == TRG_PHASE_X2 ? ctx.region_begin(TRG_PHASE_MMA_X2) : -1;
     switch (S * 2 + CG - 1) {
-        case 4: launch_mma<2, 1>(ctx, ta, tb, a); break;
-        case 5: launch_mma<2, 2>(ctx, ta, tb, a); break;
-        case 6: launch_mma<3, 1>(ctx, ta, tb, a); break;
-        case 7: launch_mma<3, 2>(ctx, ta, tb, a); break;
-        case 8: launch_mma<4, 1>(ctx, ta, tb, a); break;
-        case 9: launch_mma<4, 2>(ctx, ta, tb, a); break;
-        case 10: launch_mma<5, 1>(ctx, ta, tb, a); break;
-        case 11: launch_mma<5, 2>(ctx, ta, tb, a); break;
+        case 4: launch_mma<2, 1>(ctx, ta, tb, tbh, a); break;
+        case 5: launch_mma<2, 2>(ctx, ta, tb, tbh, a); break;
+        case 6: launch_mma<3, 1>(ctx, ta, tb, tbh, a); break;
+        case 7: launch_mma<3, 2>(ctx, ta, tb, tbh, a); break;
+        case 8: launch_mma<4, 1>(ctx, ta, tb, tbh, a); break;
+        case 9: launch_mma<4, 2>(ctx, ta, tb, tbh, a); break;
+        case 10: launch_mma<5, 1>(ctx, ta, tb, tbh, a); break;
+        case 11: launch_mma<5, 2>(ctx, ta, tb, tbh, a); break;
     }
     const double products = (double)S * (S + 1) / 2;
     ctx.region_end(tok_x2, 2.0 * (double)M * N * K, products * 2.0 * (double)M * N * Kp);
@@ -1515,8 +1510,8 @@ extern "C" int trg_gemm_noalloc(int M, int N, int K, const double* A, int lda, c
         switch (S) {
 #define TRG_NOALLOC_MMA(SS)                                                                                  \
     TRG_CUDA(cudaFuncSetAttribute(k_split_mma<SS, 1, EPI_STAGED>, cudaFuncAttributeMaxDynamicSharedMemorySize,           \
-                                  smem_bytes_for(SS, 1)));                                                   \
-    k_split_mma<SS, 1, EPI_STAGED><<<grid, THREADS, smem_bytes_for(SS, 1), stream>>>(ta, tbm, a);                        \
+                                  smem_bytes_for(SS, 1, EPI_STAGED)));                                                   \
+    k_split_mma<SS, 1, EPI_STAGED><<<grid, THREADS, smem_bytes_for(SS, 1, EPI_STAGED), stream>>>(ta, tbm, tbm, a);                        \
     break;
             case 2: TRG_NOALLOC_MMA(2)
             case 3: TRG_NOALLOC_MMA(3)

@@ -89,25 +89,19 @@ def test_split_gemm_pairs_exact_on_integers(torch, m, n, k, s):
 @pytest.mark.parametrize("m,n,k", [(257, 300, 4096), (1000, 129, 3000), (4096, 512, 2048)])
 @pytest.mark.parametrize("s", [2, 3, 4, 5])
 def test_split_gemm_pairs_match_single(torch, m, n, k, s):
-    # S = 2, 3: same products into the same accumulators in the same order,
-    # identical bits.  S = 4, 5: the pair kernel puts two single products
-    # into the other remainder accumulator and adds two products beyond the
-    # truncation, so both stay inside the error bound of the splitting.
+    # the pair kernel issues the single-CTA product table at M = 256: the same
+    # products into the same accumulators in the same order, identical bits
     rng = np.random.default_rng(m + n + k + s)
-    an = rng.standard_normal((m, k))
+    an = rng.standard_normal((m, k)) * np.exp(rng.uniform(-6, 6, size=(m, 1)))
     bn = rng.standard_normal((k, n))
     a, b = torch.from_numpy(an).cuda(), torch.from_numpy(bn).cuda()
     with Solver(0, precision="split", mma_pairs=0, split_slices=s) as s1, \
             Solver(0, precision="split", mma_pairs=1, split_slices=s) as s2:
         c1 = s1.gemm(a, b)
         c2 = s2.gemm(a, b)
-    if s <= 3:
-        assert torch.equal(c1, c2)
-    else:
-        ref = an @ bn
-        bound = _bound(an, bn, s)
-        assert np.all(np.abs(c1.cpu().numpy() - ref) <= bound)
-        assert np.all(np.abs(c2.cpu().numpy() - ref) <= bound)
+    assert torch.equal(c1, c2)
+    ref = an @ bn
+    assert np.all(np.abs(c2.cpu().numpy() - ref) <= _bound(an, bn, s))
 
 
 def test_split_gemm_zero_rows_and_tiny_values(torch):
@@ -181,3 +175,17 @@ def test_fused_handover_solve_is_bit_identical(torch):
             sv.coarse_grain(32, 12)
             res.append(sv.free_energy())
     assert res[0] == res[1] == res[2]
+
+
+@pytest.mark.parametrize("model,beta,h,dcut,nsteps", [("ising", 0.4406868, 1e-3, 32, 12), ("xy", 1.0, 0.0, 24, 8)])
+def test_split_solve_pairs_match_single(torch, model, beta, h, dcut, nsteps):
+    # every product of the solve on CTA pairs or on single CTAs: identical bits
+    out = []
+    for pairs in (0, 1):
+        with Solver(0, precision="split", mma_pairs=pairs,
+                    trunc="multiplet" if model == "xy" else "paper") as sv:
+            sv.init_tensor(model, beta, h)
+            sv.coarse_grain(dcut, nsteps)
+            out.append((sv.free_energy(), sv.tensor()))
+    assert out[0][0] == out[1][0]
+    assert np.array_equal(out[0][1], out[1][1])
