@@ -70,8 +70,7 @@ typedef struct trg_config {
     int split_slices;        /* BF16 slices per operand in TRG_SPLIT_BF16, 2..5 (default 4);
                                 the contraction products use it (see env_slices) */
     int split_from_step;     /* in TRG_SPLIT_BF16 the half-steps k <= split_from_step run in FP64
-                                (default 2: steps 1 and 2 hold bond dimensions 2 and 4, cost
-                                nothing, and their norms weigh 1/2 and 1/4 in ln Z / V) */
+                                (default 0) */
     int trunc;               /* trg_trunc (default TRG_TRUNC_PAPER) */
     double gap_tol;          /* multiplet gap, relative to lambda_1 (default 1e-6; in
                                 TRG_SPLIT_BF16 at least 2^-(8*S-12), S = the env slices) */
@@ -92,6 +91,12 @@ typedef struct trg_config {
                                 slicing pass); 2 also hands the first product over as
                                 slices; 0 always goes through FP64.  Results are identical
                                 in all three. */
+    int fp64_max_dd;         /* TRG_SPLIT_BF16: half-steps on a tensor with Dx*Dy <= fp64_max_dd
+                                (Dx*Dy*Dz on the cubic lattice) run in FP64 (default 16: the
+                                first three half-steps of a model's solve, bond dimensions 2
+                                to 4, whose norms weigh 1/2, 1/4 and 1/8 in ln Z / V; in
+                                FP64 they cost nothing and keep the split path's error in f
+                                several times lower) */
     int env_slices;          /* TRG_SPLIT_BF16: BF16 slices of the environment products and of
                                 the isometry's M.Q products, 2..5; 0 (default) = split_slices.
                                 The isometry's tolerances above then follow env_slices. */

@@ -41,6 +41,7 @@ class trg_config(ctypes.Structure):
         ("workspace_bytes", c_size_t),
         ("mma_pairs", c_int),
         ("fused_slices", c_int),
+        ("fp64_max_dd", c_int),
         ("env_slices", c_int),
     ]
 

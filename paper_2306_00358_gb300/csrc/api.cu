@@ -118,7 +118,7 @@ static HalfPlan half_step_prepare(Ctx& ctx, int dcut) {
     HalfPlan p;
     p.k = ctx.steps + 1;
     p.xdir = (p.k % 2) == 1;
-    p.precision = precision_for_step(ctx, p.k);
+    p.precision = precision_for_step(ctx, p.k, (int64_t)ctx.Dx * ctx.Dy);
     const int64_t Dx = ctx.Dx, Dy = ctx.Dy;
     View4 t = contiguous_view(ctx.T.as<double>(), Dx, Dy, Dx, Dy);
     p.r = t;
@@ -268,10 +268,12 @@ int trg_config_default(trg_config* cfg) {
     std::memset(cfg, 0, sizeof(*cfg));
     cfg->precision = TRG_FP64;
     cfg->split_slices = 4;
-    // the first two half-steps (bond dimensions 2 and 4) run in FP64: their
-    // norms weigh 1/2 and 1/4 in ln Z / V and their split products carried
-    // most of the split path's error in f (about 5x at Dcut 64), at no cost
-    cfg->split_from_step = 2;
+    cfg->split_from_step = 0;
+    // half-steps on tensors with Dx Dy <= 16 run in FP64: those of a model's
+    // first three half-steps (bond dimensions 2 to 4), whose norms weigh 1/2,
+    // 1/4 and 1/8 in ln Z / V; their split products carried most of the split
+    // path's error in f (about 5x at Dcut 64) and in FP64 they cost nothing
+    cfg->fp64_max_dd = 16;
     cfg->trunc = TRG_TRUNC_PAPER;
     cfg->gap_tol = 1e-6;
     cfg->oversample = 24;
@@ -289,7 +291,7 @@ static int validate_config(const trg_config& c) {
     if (c.precision != TRG_FP64 && c.precision != TRG_SPLIT_BF16) return TRG_EINVAL;
     if (c.split_slices < 2 || c.split_slices > 5) return TRG_EINVAL;
     if (c.env_slices != 0 && (c.env_slices < 2 || c.env_slices > 5)) return TRG_EINVAL;
-    if (c.split_from_step < 0) return TRG_EINVAL;
+    if (c.split_from_step < 0 || c.fp64_max_dd < 0) return TRG_EINVAL;
     if (c.mma_pairs != 0 && c.mma_pairs != 1) return TRG_EINVAL;
     if (c.fused_slices < 0 || c.fused_slices > 2) return TRG_EINVAL;
     if (c.trunc != TRG_TRUNC_PAPER && c.trunc != TRG_TRUNC_MULTIPLET) return TRG_EINVAL;
@@ -625,7 +627,7 @@ int trg_solve3d(trg_ctx* ctx, int model, double beta, double h, int Dcut, int ns
         const int64_t Nx = std::min<int64_t>(Dx * Dx, Dcut), Ny = std::min<int64_t>(Dy * Dy, Dcut);
         c.ensure(c.Tnext, (size_t)(Nx * Nx * Ny * Ny * Dz * Dz) * sizeof(double));
         std::vector<double> lx, ly;
-        const auto kept = trg::step3(c, v, Dcut, k, c.Tnext.as<double>(), trg::precision_for_step(c, k), lx, ly);
+        const auto kept = trg::step3(c, v, Dcut, k, c.Tnext.as<double>(), trg::precision_for_step(c, k, Dx * Dy * Dz), lx, ly);
         const int64_t kx = kept.first, ky = kept.second;
         c.phase = TRG_PHASE_NORM;
         trg::launch_normalise(c, c.Tnext.as<double>(), kx * kx * ky * ky * Dz * Dz, k, false);

@@ -138,10 +138,7 @@ void trg_server::run_request(trg_ctx*& ctx, Request* r) {
         }
         trg_set_stream(ctx, stream);
     }
-    trg_config dflt;
-    trg_config_default(&dflt);
-    int st = trg_set_precision(ctx, s.precision, s.precision == TRG_SPLIT_BF16 ? s.split_slices : 4,
-                               dflt.split_from_step);
+    int st = trg_set_precision(ctx, s.precision, s.precision == TRG_SPLIT_BF16 ? s.split_slices : 4, 0);
     if (st == TRG_OK) {
         ctx->cfg.trunc = s.trunc;
         ctx->cfg.seed = s.seed ? s.seed : 0x5EEDull;

@@ -218,7 +218,9 @@ void gemm_f64(Ctx& ctx, const GemmDesc& g);
 std::vector<int64_t> build_table(const std::vector<std::pair<int64_t, int64_t>>& modes);
 
 // ------------------------------------------------------ path pieces ----
-int precision_for_step(const Ctx& ctx, int step);
+// Arithmetic of half-step `step` on a tensor whose leg dimensions multiply to
+// dd (Dx Dy; Dx Dy Dz on the cubic lattice).
+int precision_for_step(const Ctx& ctx, int step, int64_t dd);
 // BF16 slices of the split products issued now: env_slices during the
 // environment and the isometry (when set), split_slices otherwise.
 int slices_now(const Ctx& ctx);

@@ -76,9 +76,10 @@ int slices_now(const Ctx& ctx) {
     return (env && ctx.cfg.env_slices) ? ctx.cfg.env_slices : ctx.cfg.split_slices;
 }
 
-int precision_for_step(const Ctx& ctx, int step) {
+int precision_for_step(const Ctx& ctx, int step, int64_t dd) {
     if (ctx.cfg.precision == TRG_FP64) return TRG_FP64;
-    return (step - 1 < ctx.cfg.split_from_step) ? TRG_FP64 : ctx.cfg.precision;
+    if (step - 1 < ctx.cfg.split_from_step || dd <= ctx.cfg.fp64_max_dd) return TRG_FP64;
+    return ctx.cfg.precision;
 }
 
 // M[(i,j),(k,l)] = sum_{e,f} Q[i,e,k,f] P[j,e,l,f],

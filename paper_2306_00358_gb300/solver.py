@@ -111,7 +111,7 @@ class Solver:
         """Limit of the split products' accumulator wait (0 = 2 s); see trg_set_wait_limit."""
         self._check(self._lib.trg_set_wait_limit(self._h, int(acc_wait_ns)), "trg_set_wait_limit")
 
-    def set_precision(self, precision, split_slices: int = 4, split_from_step: int = 2):
+    def set_precision(self, precision, split_slices: int = 4, split_from_step: int = 0):
         p = _PREC[precision] if isinstance(precision, str) else int(precision)
         self._check(self._lib.trg_set_precision(self._h, p, split_slices, split_from_step), "trg_set_precision")
 
