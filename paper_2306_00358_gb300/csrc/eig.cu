@@ -90,21 +90,37 @@ __global__ void __launch_bounds__(256) k_col_normalize(double* Y, int64_t n, int
 
 // Right-looking Cholesky G = L L^T of an m x m Gram matrix of unit columns.
 // Per column: warp 0 takes the pivot and scales the column (also into a
-// broadcast copy), then every warp updates trailing rows, a lane per column.
+// broadcast copy), then all threads update the trailing triangle.
 // A pivot d_j <= tau * G_jj marks column j as dependent (flags[j] = 1,
 // *nbad += 1); the pivot is then replaced by G_jj so the factorisation can
 // continue.
+// The trailing update of column j touches the elements (i, k), j < k <= i.
+// They are listed once, by k descending (k = m-1 first), so those of column
+// j are the first (m-1-j)(m-j)/2 entries: every thread takes a share and a
+// warp's FP64 instructions run on all 32 lanes (the FP64 pipe, not the
+// lanes, is what a lane-per-column layout of short rows wastes).
+__host__ __device__ constexpr int chol_table_entries(int m) { return m * (m - 1) / 2; }
 __global__ void __launch_bounds__(256) k_chol_flag(const double* G, double* Lout, int m, double tau,
                                                    int* flags, int* nbad) {
     // m rows of ld = m + 1 (an odd stride: the rows of one column fall in
-    // different banks), m of the original diagonal, m of column j
+    // different banks), m of the original diagonal, m of column j, then the
+    // trailing-element list (i << 7 | k, 16 bits each)
     extern __shared__ double L[];
     const int ld = m + 1;
     double* gd = L + m * ld;
     double* colj = gd + m;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
+    uint16_t* tab = (uint16_t*)(colj + m);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     for (int e = threadIdx.x; e < m * m; e += blockDim.x) L[(e / m) * ld + e % m] = G[e];
     for (int i = threadIdx.x; i < m; i += blockDim.x) gd[i] = G[(int64_t)i * m + i];
+    for (int e = threadIdx.x; e < chol_table_entries(m); e += blockDim.x) {
+        // group gidx = m-1-k holds the gidx+1 elements (k..m-1, k) from offset gidx(gidx+1)/2
+        int gidx = (int)((sqrtf(8.0f * (float)e + 1.0f) - 1.0f) * 0.5f);
+        while (gidx * (gidx + 1) / 2 > e) --gidx;
+        while ((gidx + 1) * (gidx + 2) / 2 <= e) ++gidx;
+        const int k = m - 1 - gidx, i = k + (e - gidx * (gidx + 1) / 2);
+        tab[e] = (uint16_t)((i << 7) | k);
+    }
     __syncthreads();
     for (int j = 0; j < m; ++j) {
         if (warp == 0) {
@@ -127,9 +143,11 @@ __global__ void __launch_bounds__(256) k_chol_flag(const double* G, double* Lout
             }
         }
         __syncthreads();
-        for (int i = j + 1 + warp; i < m; i += nwarps) {
-            const double li = colj[i];
-            for (int k = j + 1 + lane; k <= i; k += 32) L[i * ld + k] = fma(-li, colj[k], L[i * ld + k]);
+        const int cnt = (m - 1 - j) * (m - j) / 2;
+        for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
+            const unsigned t = tab[e];
+            const int i = (int)(t >> 7), k = (int)(t & 127u);
+            L[i * ld + k] = fma(-colj[i], colj[k], L[i * ld + k]);
         }
         __syncthreads();
     }
@@ -140,10 +158,12 @@ __global__ void __launch_bounds__(256) k_chol_flag(const double* G, double* Lout
 // Q = Y L^{-T} row by row, in place allowed: 32 rows per block, a lane per
 // row, the solution in shared memory.  Right-looking: after x_j is known,
 // every later column k subtracts L[k][j] x_j.  Column k belongs to warp
-// k % 4, so the four warps (and the SM's four FP64 pipes) share the updates
-// and x_j needs no reduction, one block barrier per column.
+// k % 8, so the eight warps (two per FP64 pipe, which hides the latency of
+// each one's load-FMA-store chain) share the updates and x_j needs no
+// reduction, one block barrier per column.
 constexpr int TRSM_ROWS = 32;
-constexpr int TRSM_THREADS = 128;
+constexpr int TRSM_THREADS = 256;
+constexpr int TRSM_WARPS = TRSM_THREADS / 32;
 __global__ void __launch_bounds__(TRSM_THREADS) k_trsm_rows(double* Y, const double* Lg, int64_t n, int m) {
     extern __shared__ double L[];   // m*m, m inverse diagonals, TRSM_ROWS rows of m + 1, 2 x TRSM_ROWS x_j
     double* dinv = L + m * m;
@@ -161,15 +181,15 @@ __global__ void __launch_bounds__(TRSM_THREADS) k_trsm_rows(double* Y, const dou
     double* y = rows + lane * (m + 1);
     for (int j = 0; j < m; ++j) {
         double* xs = xb + (j & 1) * TRSM_ROWS;
-        if (warp == (j & 3)) {
+        if (warp == (j & (TRSM_WARPS - 1))) {
             const double x = y[j] * dinv[j];
             y[j] = x;
             xs[lane] = x;
         }
         __syncthreads();
         const double x = xs[lane];
-        int k = j + 1 + ((warp - (j + 1)) & 3);      // first column > j owned by this warp
-        for (; k < m; k += 4) y[k] = fma(-L[k * m + j], x, y[k]);
+        int k = j + 1 + ((warp - (j + 1)) & (TRSM_WARPS - 1));   // first column > j owned by this warp
+        for (; k < m; k += TRSM_WARPS) y[k] = fma(-L[k * m + j], x, y[k]);
     }
     __syncthreads();
     for (int e = threadIdx.x; e < m * TRSM_ROWS; e += blockDim.x) {
@@ -182,7 +202,7 @@ __global__ void __launch_bounds__(TRSM_THREADS) k_trsm_rows(double* Y, const dou
 // slab of rows into its own m x m partial (rows staged in shared memory);
 // k_gram_reduce adds the partials in slab order (deterministic).
 __global__ void __launch_bounds__(256) k_gram_partial(const double* A, const double* B, int64_t n, int m,
-                                                      int64_t rows_per_cta, double* part) {
+                                                      int64_t rows_per_cta, double* part, int sym) {
     extern __shared__ double sh[];   // rows_per_cta x m for A, then for B
     const int64_t r0 = blockIdx.x * rows_per_cta;
     const int64_t nr = max((int64_t)0, min(rows_per_cta, n - r0));
@@ -195,8 +215,22 @@ __global__ void __launch_bounds__(256) k_gram_partial(const double* A, const dou
     }
     __syncthreads();
     double* P = part + (int64_t)blockIdx.x * m * m;
-    for (int e = threadIdx.x; e < m * m; e += 256) {
-        const int i = e / m, j = e % m;
+    // A = B: the partial is symmetric and the products of (j, i) are those
+    // of (i, j), so the upper triangle is mirrored (identical bits)
+    const int ne = sym ? m * (m + 1) / 2 : m * m;
+    for (int e0 = threadIdx.x; e0 < ne; e0 += 256) {
+        int i, j;
+        if (sym) {
+            // e0 -> (i, j), i <= j, row-major over the upper triangle
+            i = (int)(((2.0f * m + 1.0f) - sqrtf((2.0f * m + 1.0f) * (2.0f * m + 1.0f) - 8.0f * (float)e0)) * 0.5f);
+            while (i > 0 && i * m - i * (i - 1) / 2 > e0) --i;
+            while ((i + 1) * m - (i + 1) * i / 2 <= e0) ++i;
+            j = i + (e0 - (i * m - i * (i - 1) / 2));
+        } else {
+            i = e0 / m;
+            j = e0 % m;
+        }
+        const int e = i * m + j;
         double s0 = 0.0, s1 = 0.0;
         int64_t r = 0;
         for (; r + 1 < nr; r += 2) {
@@ -205,13 +239,15 @@ __global__ void __launch_bounds__(256) k_gram_partial(const double* A, const dou
         }
         if (r < nr) s0 = fma(As[r * m + i], Bs[r * m + j], s0);
         P[e] = s0 + s1;
+        if (sym && i != j) P[j * m + i] = s0 + s1;
     }
 }
 
-__global__ void k_gram_reduce(const double* part, int nparts, int m, double* G) {
+__global__ void __launch_bounds__(64) k_gram_reduce(const double* part, int nparts, int m, double* G) {
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= m * m) return;
     double s = 0.0;
+#pragma unroll 8
     for (int p = 0; p < nparts; ++p) s += part[(int64_t)p * m * m + e];
     G[e] = s;
 }
@@ -467,7 +503,7 @@ static size_t jacobi_smem(int m) {
 }
 
 static size_t chol_smem(int m) {
-    return (size_t)m * (m + 1) * 8 + (size_t)m * 16;
+    return (size_t)m * (m + 1) * 8 + (size_t)m * 16 + (size_t)chol_table_entries(m) * 2 + 16;
 }
 
 static size_t trsm_smem(int m) {
@@ -491,9 +527,9 @@ static void gram(Ctx& ctx, const double* A, const double* B, int64_t n, int m, d
         TRG_CUDA(cudaFuncSetAttribute((const void*)k_gram_partial, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       100 * 1024));
     });
-    k_gram_partial<<<nparts, 256, smem, ctx.stream>>>(A, B, n, m, rows_c, ctx.f64_partial.as<double>());
+    k_gram_partial<<<nparts, 256, smem, ctx.stream>>>(A, B, n, m, rows_c, ctx.f64_partial.as<double>(), A == B ? 1 : 0);
     TRG_LAUNCHED(ctx);
-    k_gram_reduce<<<(m * m + 255) / 256, 256, 0, ctx.stream>>>(ctx.f64_partial.as<double>(), nparts, m, G);
+    k_gram_reduce<<<(m * m + 63) / 64, 64, 0, ctx.stream>>>(ctx.f64_partial.as<double>(), nparts, m, G);
     TRG_LAUNCHED(ctx);
 }
 static void times_small(Ctx& ctx, const double* A, const double* W, int64_t n, int m, double* C) {
