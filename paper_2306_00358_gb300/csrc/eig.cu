@@ -101,7 +101,7 @@ __global__ void __launch_bounds__(256) k_col_normalize(double* Y, int64_t n, int
 // lanes, is what a lane-per-column layout of short rows wastes).
 __host__ __device__ constexpr int chol_table_entries(int m) { return m * (m - 1) / 2; }
 __global__ void __launch_bounds__(256) k_chol_flag(const double* G, double* Lout, int m, double tau,
-                                                   int* flags, int* nbad) {
+                                                   int* flags, int* nbad, double* pivmin_out) {
     // m rows of ld = m + 1 (an odd stride: the rows of one column fall in
     // different banks), m of the original diagonal, m of column j, then the
     // trailing-element list (i << 7 | k, 16 bits each)
@@ -122,11 +122,13 @@ __global__ void __launch_bounds__(256) k_chol_flag(const double* G, double* Lout
         tab[e] = (uint16_t)((i << 7) | k);
     }
     __syncthreads();
+    double pivmin = 1.0;    // smallest d_j / G_jj (thread 0): 1 / pivmin bounds cond(Y)^2 from below
     for (int j = 0; j < m; ++j) {
         if (warp == 0) {
             double d = L[j * ld + j];
             if (lane == 0) {
                 const double gjj = gd[j];
+                pivmin = fmin(pivmin, (gjj > 0.0 && isfinite(d)) ? d / gjj : 0.0);
                 if (!(d > tau * gjj) || !isfinite(d)) {
                     flags[j] = 1;
                     atomicAdd(nbad, 1);
@@ -153,6 +155,7 @@ __global__ void __launch_bounds__(256) k_chol_flag(const double* G, double* Lout
     }
     for (int e = threadIdx.x; e < m * m; e += blockDim.x)
         Lout[e] = ((e % m) <= (e / m)) ? L[(e / m) * ld + e % m] : 0.0;
+    if (threadIdx.x == 0 && pivmin_out) *pivmin_out = pivmin;
 }
 
 // Q = Y L^{-T} row by row, in place allowed: 32 rows per block, a lane per
@@ -541,9 +544,18 @@ static void times_small(Ctx& ctx, const double* A, const double* W, int64_t n, i
     gemm(ctx, g, TRG_FP64);
 }
 
-// Orthonormalise the columns of Y in place (two Cholesky-QR passes).
+// Orthonormalise the columns of Y in place (two Cholesky-QR passes).  After
+// one pass Q^T Q = I to about eps / min_j(d_j / G_jj) (the pivots of the
+// column-normalised Gram matrix bound its conditioning); when the next step
+// is another power step rather than a Rayleigh-Ritz step (`power_next`),
+// which needs only a well-conditioned basis, a clean first pass with
+// pivots above PASS2_PIVMIN is enough and the second pass is skipped.
+constexpr double PASS2_PIVMIN = 1e-3;
 static void orthonormalise(Ctx& ctx, double* Y, int64_t n, int m, double* G, double* L, int* flags,
-                           int* nbad, uint64_t seed, uint64_t& salt) {
+                           int* nbad, uint64_t seed, uint64_t& salt, bool power_next = false) {
+    double* pivmin = ctx.scal.as<double>() + SC_PIVMIN;
+    double pm = 0.0;
+    bool first_clean = true;    // the first pass needed no column repair
     for (int pass = 0; pass < 2; ++pass) {
         int attempt = 0;
         for (;; ++attempt) {
@@ -552,12 +564,14 @@ static void orthonormalise(Ctx& ctx, double* Y, int64_t n, int m, double* G, dou
             TRG_LAUNCHED(ctx);
             gram(ctx, Y, Y, n, m, G, TRG_FP64);
             k_chol_flag<<<1, 256, chol_smem(m), ctx.stream>>>(G, L, m, pass == 0 ? 1e-8 : 1e-12, flags,
-                                                                     nbad);
+                                                                     nbad, pivmin);
             TRG_LAUNCHED(ctx);
             int hb = 0;
             TRG_CUDA(cudaMemcpyAsync(&hb, nbad, sizeof(int), cudaMemcpyDeviceToHost, ctx.stream));
+            TRG_CUDA(cudaMemcpyAsync(&pm, pivmin, sizeof(double), cudaMemcpyDeviceToHost, ctx.stream));
             TRG_CUDA(cudaStreamSynchronize(ctx.stream));
             if (hb == 0) break;
+            if (pass == 0) first_clean = false;
             ctx.counters[4] += (uint64_t)hb;
             if (attempt >= 16) fail(TRG_ENUMERIC, "Cholesky-QR: could not complete a basis");
             dim3 grid((unsigned)std::min<int64_t>((n + 255) / 256, 64), (unsigned)m);
@@ -567,6 +581,10 @@ static void orthonormalise(Ctx& ctx, double* Y, int64_t n, int m, double* G, dou
         k_trsm_rows<<<(unsigned)((n + TRSM_ROWS - 1) / TRSM_ROWS), TRSM_THREADS, trsm_smem(m), ctx.stream>>>(Y, L, n,
                                                                                                           m);
         TRG_LAUNCHED(ctx);
+        if (pass == 0 && power_next && first_clean && pm >= PASS2_PIVMIN) {
+            ctx.counters[5] += 1;
+            return;
+        }
     }
 }
 
@@ -637,7 +655,6 @@ int isometry(Ctx& ctx, const double* M, int64_t n, int dcut, double* U, std::vec
         g.C = Y; g.c_m = ctx.table({{n, 1}}); g.c_n = ctx.table({{m, n}}); g.beta = 0.0;
         gemm(ctx, g, precision);
     };
-    orthonormalise(ctx, Q, n, m, G, L, flags, nbad, seed, salt);
     // The number of products that reached the tolerance in the previous solve
     // of this direction (same sizes) is the plan: the spectra of successive
     // same-direction environments are close, and a random start needs about
@@ -645,12 +662,15 @@ int isometry(Ctx& ctx, const double* M, int64_t n, int dcut, double* U, std::vec
     // a first, FP32-only Rayleigh-Ritz that measures the convergence rate.
     Ctx::EigHint& hint = ctx.eig_hint[step & 1];
     const bool have_hint = hint.n == n && hint.m == m && hint.precision == precision && hint.products > 0;
+    // the start block is followed by power steps unless the first step is a
+    // Rayleigh-Ritz step (no plan and m = n)
+    orthonormalise(ctx, Q, n, m, G, L, flags, nbad, seed, salt, have_hint || m < n);
     int applied = 0;                 // products of M in the span of Q
     if (!have_hint) {
         for (int pre = 0; pre < 2 && m < n; ++pre) {
             apply_m();
             std::swap(Q, Y);
-            orthonormalise(ctx, Q, n, m, G, L, flags, nbad, seed, salt);
+            orthonormalise(ctx, Q, n, m, G, L, flags, nbad, seed, salt, pre == 0);
             ++applied;
         }
     }
@@ -677,7 +697,7 @@ int isometry(Ctx& ctx, const double* M, int64_t n, int dcut, double* U, std::vec
         if (pending > 0) {
             apply_m();
             std::swap(Q, Y);
-            orthonormalise(ctx, Q, n, m, G, L, flags, nbad, seed, salt);
+            orthonormalise(ctx, Q, n, m, G, L, flags, nbad, seed, salt, pending > 1);
             --pending;
             ++since_rr;
             ++applied;
@@ -758,7 +778,7 @@ int isometry(Ctx& ctx, const double* M, int64_t n, int dcut, double* U, std::vec
         // next block: orth(Y W) = orth(M Q W), same span as M Q
         ++applied;
         std::swap(Q, Z);
-        orthonormalise(ctx, Q, n, m, G, L, flags, nbad, seed, salt);
+        orthonormalise(ctx, Q, n, m, G, L, flags, nbad, seed, salt, pending > 0);
     }
     fail(TRG_ENUMERIC, "subspace iteration did not converge");
 }

@@ -152,6 +152,7 @@ enum : int {
     SC_TRACE = 3,     // last trace
     SC_RES = 4,       // max Ritz residual / lambda_1 (subspace iteration)
     SC_TRACE_IMP = 5, // last trace of the impure tensor
+    SC_PIVMIN = 6,    // smallest pivot ratio d_j / G_jj of the last Cholesky-QR pass
     SC_COUNT = 8
 };
 
