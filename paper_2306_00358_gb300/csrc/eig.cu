@@ -344,31 +344,29 @@ __device__ int jacobi_sweeps(T* H, int ld, T* W, int m, T tol, int max_sweeps, T
 // Rayleigh-Ritz eigensolve of the symmetric m x m matrix Hg (global), in
 // two precisions:
 //  1. FP32 Jacobi on H / max|H| to a relative threshold of 1e-6 (the FP32
-//     pipe is ~60x the FP64 pipe on this part); rotations accumulate in W32;
+//     pipe is ~60x the FP64 pipe on this part); rotations accumulate in W32
+//     (k_rr_fp32, one CTA);
 //  2. W = W32 in FP64, re-orthonormalised by Cholesky-QR (W^T W = L L^T,
-//     W <- W L^-T), and H' = W^T H W formed in FP64;
-//  3. FP64 Jacobi sweeps on H' (it starts ~1e-6 off diagonal, so two or three
-//     quadratically convergent sweeps finish it), W <- W J.
+//     W <- W L^-T), and H' = W^T H W formed in FP64: m x m products on many
+//     SMs (k_small_tn, k_small_nn), the Cholesky and the triangular solve of
+//     the Cholesky-QR path (k_chol_flag, k_trsm_rows);
+//  3. FP64 Jacobi sweeps on H' (it starts ~1e-6 off diagonal, so one
+//     quadratically convergent sweep and a confirming one finish it),
+//     W <- W J (k_rr_fp64, one CTA).
 // Output: theta sorted descending, W (column-major, global) in that order.
-// Shared memory: H (m rows of ld = m + 1 doubles: the odd stride puts the
-// rows of one column in different banks, so the column updates are
-// conflict-free) + m*ld doubles of scratch (H32 with the same stride and W32,
-// later the Gram/Cholesky matrix) + small arrays.
-__global__ void __launch_bounds__(512) k_jacobi(const double* Hg, int m, double tol, int max_sweeps,
-                                                double* theta, double* Wout, double* T1, int* status,
-                                                int* sweeps_out, int fp64_sweeps) {
+// Shared memory of the one-CTA kernels: H (m rows of ld = m + 1 doubles: the
+// odd stride puts the rows of one column in different banks, so the column
+// updates are conflict-free) + m*ld doubles of scratch + small arrays.
+__global__ void __launch_bounds__(512) k_rr_fp32(const double* Hg, int m, double* Hsym, double* Wout,
+                                                 int* sweeps_out) {
     extern __shared__ double sm[];
     const int mp = m + (m & 1);
     const int ld = m + 1;
-    double* H = sm;                            // m*ld
-    double* R2 = H + m * ld;                   // m*ld doubles of scratch
-    float* H32 = (float*)R2;                   // m*ld floats
+    float* H32 = (float*)sm;                   // m*ld floats
     float* W32 = H32 + m * ld;                 // m*m floats
-    double* cs64 = R2 + m * ld;                // mp
-    float* cs32 = (float*)(cs64 + mp);         // mp
+    float* cs32 = W32 + m * m;                 // mp
     int* rot = (int*)(cs32 + mp + (mp & 1));   // 1
-    int* perm = rot + 2;                       // m
-    int* pq = perm + m + (m & 1);              // mp: the pairs of the current round
+    int* pq = rot + 2;                         // mp: the pairs of the current round
     __shared__ double hmax_s;
     if (threadIdx.x == 0) hmax_s = 0.0;
     __syncthreads();
@@ -376,7 +374,7 @@ __global__ void __launch_bounds__(512) k_jacobi(const double* Hg, int m, double 
     for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
         const int i = e / m, j = e % m;
         const double v = 0.5 * (Hg[(int64_t)i * m + j] + Hg[(int64_t)j * m + i]);
-        H[i * ld + j] = v;
+        Hsym[e] = v;
         lmax = fmax(lmax, fabs(v));
     }
     for (int o = 16; o > 0; o >>= 1) lmax = fmax(lmax, __shfl_xor_sync(0xffffffffu, lmax, o));
@@ -385,86 +383,76 @@ __global__ void __launch_bounds__(512) k_jacobi(const double* Hg, int m, double 
     const double hscale = hmax_s > 0.0 ? 1.0 / hmax_s : 1.0;
     for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
         const int i = e / m, j = e % m;
-        H32[i * ld + j] = (float)(H[i * ld + j] * hscale);
+        H32[i * ld + j] = (float)(0.5 * (Hg[(int64_t)i * m + j] + Hg[(int64_t)j * m + i]) * hscale);
         W32[e] = (i == j) ? 1.0f : 0.0f;
     }
     __syncthreads();
-    // 1. FP32 sweeps
     const int s32 = jacobi_sweeps<float>(H32, ld, W32, m, 1e-6f, 40, cs32, rot, pq);
-    // 2. W (FP64) = W32, then Cholesky-QR of its columns
     for (int e = threadIdx.x; e < m * m; e += blockDim.x) Wout[e] = (double)W32[e];
-    __syncthreads();
-    double* G = R2;   // the FP32 arrays are no longer needed
+    if (threadIdx.x == 0 && sweeps_out) atomicAdd(sweeps_out, s32);
+}
+
+// C[i][j] = sum_r A[i*m + r] B[j*m + r] (the columns of two column-major m x
+// m blocks): a CTA per row i, a thread per column j, the sum in order of r.
+__global__ void __launch_bounds__(128) k_small_tn(const double* A, const double* B, int m, double* C) {
+    const int i = blockIdx.x;
+    for (int j = threadIdx.x; j < m; j += blockDim.x) {
+        double a = 0.0;
+        for (int r = 0; r < m; ++r) a = fma(A[(int64_t)i * m + r], B[(int64_t)j * m + r], a);
+        C[(int64_t)i * m + j] = a;
+    }
+}
+
+// (H W)[r][j] = sum_k H[r*m + k] W[j*m + k] (row-major H, column-major W),
+// stored column-major: C[j*m + r].
+__global__ void __launch_bounds__(128) k_small_nn(const double* H, const double* W, int m, double* C) {
+    const int r = blockIdx.x;
+    for (int j = threadIdx.x; j < m; j += blockDim.x) {
+        double a = 0.0;
+        for (int k = 0; k < m; ++k) a = fma(H[(int64_t)r * m + k], W[(int64_t)j * m + k], a);
+        C[(int64_t)j * m + r] = a;
+    }
+}
+
+// Step 3 of the Rayleigh-Ritz solve: H = (G + G^T) / 2, FP64 sweeps from W,
+// then theta and W sorted by descending theta (ties keep index order).
+__global__ void __launch_bounds__(512) k_rr_fp64(const double* G, int m, double tol, int max_sweeps,
+                                                 double* theta, double* Wout, int* status, int* sweeps_out,
+                                                 int fp64_sweeps) {
+    extern __shared__ double sm[];
+    const int mp = m + (m & 1);
+    const int ld = m + 1;
+    double* H = sm;                            // m*ld
+    double* Ws = H + m * ld;                   // m*m (W, accumulated)
+    double* cs64 = Ws + m * ld;                // mp
+    int* rot = (int*)(cs64 + mp);              // 1
+    int* perm = rot + 2;                       // m
+    int* pq = perm + m + (m & 1);              // mp
     for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
         const int i = e / m, j = e % m;
-        double a = 0.0;
-        for (int r = 0; r < m; ++r) a = fma(Wout[(int64_t)i * m + r], Wout[(int64_t)j * m + r], a);
-        G[e] = a;
+        H[i * ld + j] = 0.5 * (G[(int64_t)i * m + j] + G[(int64_t)j * m + i]);
+        Ws[e] = Wout[e];
     }
     __syncthreads();
-    for (int j = 0; j < m; ++j) {                  // left-looking Cholesky, in place (lower)
-        if (threadIdx.x == 0) {
-            double d = G[j * m + j];
-            for (int k = 0; k < j; ++k) d = fma(-G[j * m + k], G[j * m + k], d);
-            G[j * m + j] = sqrt(fmax(d, 1e-300));
-        }
-        __syncthreads();
-        const double ljj = G[j * m + j];
-        for (int i = j + 1 + threadIdx.x; i < m; i += blockDim.x) {
-            double a = G[i * m + j];
-            for (int k = 0; k < j; ++k) a = fma(-G[i * m + k], G[j * m + k], a);
-            G[i * m + j] = a / ljj;
-        }
-        __syncthreads();
-    }
-    for (int r = threadIdx.x; r < m; r += blockDim.x) {   // W <- W L^-T, row by row
-        for (int j = 0; j < m; ++j) {
-            double a = Wout[(int64_t)j * m + r];
-            for (int k = 0; k < j; ++k) a = fma(-G[j * m + k], Wout[(int64_t)k * m + r], a);
-            Wout[(int64_t)j * m + r] = a / G[j * m + j];
-        }
-    }
-    __syncthreads();
-    // H' = W^T H W  (T1 = H W in global scratch, then into H)
-    for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
-        const int r = e / m, j = e % m;
-        double a = 0.0;
-        for (int k = 0; k < m; ++k) a = fma(H[r * ld + k], Wout[(int64_t)j * m + k], a);
-        T1[(int64_t)r * m + j] = a;
-    }
-    __syncthreads();
-    for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
-        const int i = e / m, j = e % m;
-        double a = 0.0;
-        for (int r = 0; r < m; ++r) a = fma(Wout[(int64_t)i * m + r], T1[(int64_t)r * m + j], a);
-        G[e] = a;
-    }
-    __syncthreads();
-    for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
-        const int i = e / m, j = e % m;
-        H[i * ld + j] = 0.5 * (G[i * m + j] + G[j * m + i]);
-    }
-    __syncthreads();
-    // 3. FP64 sweeps (skipped for a rough Rayleigh-Ritz far from convergence:
-    //    then theta is the diagonal of H' and W the re-orthonormalised W32).
-    //    W is accumulated in shared memory (the scratch is free by now).
-    double* Ws = R2;
-    for (int e = threadIdx.x; e < m * m; e += blockDim.x) Ws[e] = Wout[e];
-    __syncthreads();
+    // (skipped for a rough Rayleigh-Ritz far from convergence: then theta is
+    // the diagonal of H' and W the re-orthonormalised W32)
     const int s64 = fp64_sweeps ? jacobi_sweeps<double>(H, ld, Ws, m, tol, max_sweeps, cs64, rot, pq) : 0;
+    // rank of each diagonal value, descending; ties by index
+    for (int i = threadIdx.x; i < m; i += blockDim.x) {
+        const double hi = H[i * ld + i];
+        int r = 0;
+        for (int j = 0; j < m; ++j) {
+            const double hj = H[j * ld + j];
+            r += (hj > hi || (hj == hi && j < i)) ? 1 : 0;
+        }
+        perm[r] = i;
+    }
     if (threadIdx.x == 0) {
         if (s64 > max_sweeps) atomicOr(status, ST_EIG_NOCONV);
-        if (sweeps_out) { atomicAdd(sweeps_out, s32); atomicAdd(sweeps_out + 1, s64); }
-        for (int i = 0; i < m; ++i) perm[i] = i;
-        for (int i = 0; i < m; ++i) {
-            int best = i;
-            for (int j = i + 1; j < m; ++j)
-                if (H[perm[j] * ld + perm[j]] > H[perm[best] * ld + perm[best]]) best = j;
-            const int x = perm[i]; perm[i] = perm[best]; perm[best] = x;
-        }
-        for (int i = 0; i < m; ++i) theta[i] = H[perm[i] * ld + perm[i]];
+        if (sweeps_out) atomicAdd(sweeps_out + 1, s64);
     }
     __syncthreads();
+    for (int i = threadIdx.x; i < m; i += blockDim.x) theta[i] = H[perm[i] * ld + perm[i]];
     for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
         const int col = e / m, row = e % m;
         Wout[e] = Ws[perm[col] * m + row];
@@ -500,9 +488,14 @@ __global__ void k_to_isometry(const double* QW, int64_t n, int dn, double* U) {
 
 }  // namespace
 
-static size_t jacobi_smem(int m) {
+static size_t rr32_smem(int m) {
     const int mp = m + (m & 1);
-    return (size_t)2 * m * (m + 1) * 8 + (size_t)mp * 8 + (size_t)(mp + 2) * 4 + (size_t)(m + 4) * 4 + (size_t)mp * 4 + 64;
+    return (size_t)m * (m + 1) * 4 + (size_t)m * m * 4 + (size_t)(mp + 2) * 4 + (size_t)(mp + 4) * 4 + 64;
+}
+
+static size_t rr64_smem(int m) {
+    const int mp = m + (m & 1);
+    return (size_t)2 * m * (m + 1) * 8 + (size_t)mp * 8 + (size_t)(m + 4) * 4 + (size_t)mp * 4 + 64;
 }
 
 static size_t chol_smem(int m) {
@@ -600,11 +593,12 @@ int isometry(Ctx& ctx, const double* M, int64_t n, int dcut, double* U, std::vec
     std::call_once(once, [] {
         set_smem((const void*)k_chol_flag, chol_smem(MAX_M));
         set_smem((const void*)k_trsm_rows, trsm_smem(MAX_M));
-        set_smem((const void*)k_jacobi, jacobi_smem(MAX_M));
+        set_smem((const void*)k_rr_fp32, rr32_smem(MAX_M));
+        set_smem((const void*)k_rr_fp64, rr64_smem(MAX_M));
     });
     // buffers: Q, Y, Z, QW (n x m each); G, L, W (m x m); theta (m)
     ctx.ensure(ctx.eig, (size_t)(4 * n * m) * sizeof(double));
-    ctx.ensure(ctx.eig_small, (size_t)(3 * m * m + 2 * m + 8) * sizeof(double));
+    ctx.ensure(ctx.eig_small, (size_t)(6 * m * m + 2 * m + 8) * sizeof(double));
     ctx.ensure(ctx.flags, (size_t)(m + 8) * sizeof(int));
     double* Q = ctx.eig.as<double>();
     double* Y = Q + n * m;
@@ -614,6 +608,9 @@ int isometry(Ctx& ctx, const double* M, int64_t n, int dcut, double* U, std::vec
     double* L = G + m * m;
     double* W = L + m * m;
     double* theta = W + m * m;
+    double* Hs = theta + 2 * m + 8;    // Rayleigh-Ritz scratch: symmetrised H, H W, Gram matrices
+    double* T1 = Hs + m * m;
+    double* G2 = T1 + m * m;
     int* flags = ctx.flags.as<int>();
     int* nbad = flags + m;
     int* sweeps = flags + m + 2;   // [0] FP32 sweeps, [1] FP64 sweeps of the last Rayleigh-Ritz
@@ -675,7 +672,6 @@ int isometry(Ctx& ctx, const double* M, int64_t n, int dcut, double* U, std::vec
         }
     }
 
-    const size_t jac_smem = jacobi_smem(m);
     // Split products carry ~2^-(8S-1) relative error, which floors the Ritz
     // residual; f is insensitive to residuals far above that floor (1e-6
     // moves f by ~1e-12 on the Ising workloads), so stop at 2^-(8S-10).
@@ -720,8 +716,24 @@ int isometry(Ctx& ctx, const double* M, int64_t n, int dcut, double* U, std::vec
         // 2^-(8S-10)) the first FP64 sweep already reaches jtol, which saves a
         // whole sweep of rotations.
         const double jtol = std::max(1e-13, 1e-3 * tol);
-        k_jacobi<<<1, 512, jac_smem, ctx.stream>>>(G, m, jtol, 60, theta, W, L, status, sweeps, full);
-        TRG_LAUNCHED(ctx);
+        {
+            // the Rayleigh-Ritz solve of G = Q^T M Q into theta, W (see k_rr_fp32)
+            k_rr_fp32<<<1, 512, rr32_smem(m), ctx.stream>>>(G, m, Hs, W, sweeps);
+            TRG_LAUNCHED(ctx);
+            k_small_tn<<<m, 128, 0, ctx.stream>>>(W, W, m, G2);
+            TRG_LAUNCHED(ctx);
+            k_chol_flag<<<1, 256, chol_smem(m), ctx.stream>>>(G2, L, m, 0.0, flags, nbad, nullptr);
+            TRG_LAUNCHED(ctx);
+            k_trsm_rows<<<(unsigned)((m + TRSM_ROWS - 1) / TRSM_ROWS), TRSM_THREADS, trsm_smem(m), ctx.stream>>>(
+                W, L, m, m);
+            TRG_LAUNCHED(ctx);
+            k_small_nn<<<m, 128, 0, ctx.stream>>>(Hs, W, m, T1);
+            TRG_LAUNCHED(ctx);
+            k_small_tn<<<m, 128, 0, ctx.stream>>>(W, T1, m, G2);
+            TRG_LAUNCHED(ctx);
+            k_rr_fp64<<<1, 512, rr64_smem(m), ctx.stream>>>(G2, m, jtol, 60, theta, W, status, sweeps, full);
+            TRG_LAUNCHED(ctx);
+        }
         times_small(ctx, Y, W, n, m, Z);
         times_small(ctx, Q, W, n, m, QW);
         TRG_CUDA(cudaMemsetAsync(res_slot, 0, sizeof(double), ctx.stream));
