@@ -83,6 +83,9 @@ def parse():
     ap.add_argument("--rate", type=float, default=2.0, help="serve: mean arrivals per second")
     ap.add_argument("--slots", type=int, default=16)
     ap.add_argument("--policy", default="fifo", choices=["fifo", "shortest"], help="serve: admission order")
+    ap.add_argument("--fp64-sample", type=int, default=0,
+                    help="serve: time this many sampled requests (Dcut <= 48) as serial plain FP64 solves, and the "
+                         "FP64 seconds per half-step of each (model, Dcut) of the stream, as the serial comparator")
     ap.add_argument("--seed", type=int, default=1234)
     return ap.parse_args()
 
@@ -685,13 +688,84 @@ def run_serve(args):
     by_d = {}
     for spec, r in zip(specs, res):
         by_d.setdefault(spec.dcut, []).append(r["seconds_queued"] + r["seconds_run"])
-    print(json.dumps({"mode": "serve", "policy": args.policy, "requests": len(specs), "rate_per_s": args.rate,
-                      "slots": args.slots,
-                      "ok": sum(r["status"] == 0 for r in res), "wall_s": wall,
-                      "p50_latency_s": float(np.percentile(lat, 50)), "p99_latency_s": float(np.percentile(lat, 99)),
-                      "solves_per_s": st["solves_per_s"], "peak_admitted_bytes": st["peak_bytes"],
-                      "p50_by_dcut": {d: float(np.percentile(v, 50)) for d, v in sorted(by_d.items())}}),
-          flush=True)
+    line = {"mode": "serve", "policy": args.policy, "requests": len(specs), "rate_per_s": args.rate,
+            "slots": args.slots, "mix": "config 5: Ising:XY 0.7:0.3, Dcut {16..96} weighted .3/.25/.2/.15/.07/.03, "
+                                        "h in {0,1e-3,1e-2}, 20-40 half-steps, 150 GB budget, seed %d" % args.seed,
+            "ok": sum(r["status"] == 0 for r in res), "wall_s": wall,
+            "p50_latency_s": float(np.percentile(lat, 50)), "p99_latency_s": float(np.percentile(lat, 99)),
+            "solves_per_s": st["solves_per_s"], "peak_admitted_bytes": st["peak_bytes"],
+            "p50_by_dcut": {d: float(np.percentile(v, 50)) for d, v in sorted(by_d.items())}}
+    if args.fp64_sample > 0:
+        line["serial_fp64"] = serial_fp64_comparator(specs, res, args.fp64_sample, args.seed)
+    print(json.dumps(line), flush=True)
+
+
+def _fp64_seconds_per_step(model, dcut, beta):
+    """Steady-state seconds per half-step of a plain FP64 solve (CUDA events
+    over two half-steps once the bond dimension has reached Dcut)."""
+    import torch
+
+    from paper_2306_00358_gb300 import Solver
+    stream = torch.cuda.current_stream()
+    with Solver(0, stream=stream, precision="fp64", trunc="multiplet" if model == "xy" else "paper") as s:
+        s.init_tensor(model, beta, 0.0)
+        while True:
+            _, dx, dy, _ = s.state()
+            if min(dx, dy) >= min(dcut, 64) or s.state()[0] >= 8:
+                break
+            s.coarse_grain(dcut, 1)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        s.coarse_grain(dcut, 2)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / 2e3
+
+
+def serial_fp64_comparator(specs, res, sample, seed):
+    """The serial plain-FP64 comparator of the served stream: (a) a sample of
+    the requests with Dcut <= 48, solved one after another in FP64 and timed
+    whole, beside their served latencies; (b) the stream's serial FP64 time,
+    sum over requests of half-steps x the measured FP64 seconds per
+    steady-state half-step of that (model, Dcut) (Dcut 96 carried from 64 by
+    the D^7 cost of the contraction, labelled so)."""
+    import numpy as np
+    import torch
+
+    from paper_2306_00358_gb300 import Solver
+    rng = np.random.default_rng(seed + 1)
+    small = [i for i, s in enumerate(specs) if s.dcut <= 48]
+    pick = sorted(rng.choice(small, size=min(sample, len(small)), replace=False).tolist()) if small else []
+    t_fp64, t_served = 0.0, 0.0
+    for i in pick:
+        s = specs[i]
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        with Solver(0, precision="fp64", trunc=s.trunc) as sv:
+            sv.init_tensor(s.model, s.beta, s.h)
+            sv.coarse_grain(s.dcut, s.nsteps)
+            sv.free_energy()
+        t_fp64 += time.perf_counter() - t0
+        t_served += res[i]["seconds_run"]
+    per_step, derived = {}, {}
+    for s in specs:
+        key = (s.model, s.dcut)
+        if key in per_step:
+            continue
+        if s.dcut <= 64:
+            per_step[key] = _fp64_seconds_per_step(s.model, s.dcut, s.beta)
+    for s in specs:
+        key = (s.model, s.dcut)
+        if key not in per_step:
+            base = per_step.get((s.model, 64)) or _fp64_seconds_per_step(s.model, 64, s.beta)
+            per_step[(s.model, 64)] = base
+            per_step[key] = base * (s.dcut / 64.0) ** 7
+            derived[f"{s.model}_{s.dcut}"] = "carried from Dcut 64 by (D/64)^7"
+    total = sum(s.nsteps * per_step[(s.model, s.dcut)] for s in specs)
+    return {"sample_requests": len(pick), "sample_fp64_serial_s": t_fp64,
+            "sample_split_run_s": t_served,
+            "fp64_s_per_half_step": {f"{m}_{d}": v for (m, d), v in sorted(per_step.items())},
+            "derived": derived, "stream_fp64_serial_s": total}
 
 
 def run_potts(args):

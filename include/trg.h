@@ -100,6 +100,11 @@ typedef struct trg_config {
     int env_slices;          /* TRG_SPLIT_BF16: BF16 slices of the environment products and of
                                 the isometry's M.Q products, 2..5; 0 (default) = split_slices.
                                 The isometry's tolerances above then follow env_slices. */
+    int autotune;            /* TRG_SPLIT_BF16: 1 (default) times the launch choices (one CTA or
+                                a CTA pair per tile, tile-group width) on the first product of
+                                each shape above ~1e9 multiply-adds and keeps the fastest in a
+                                process-wide table; 0 takes the model choice.  Every choice
+                                gives identical bits. */
 } trg_config;
 
 typedef struct trg_ctx trg_ctx;
@@ -479,7 +484,8 @@ int trg_profile_read(trg_ctx* ctx, int phase, trg_phase_stats* out);
 /* Diagnostic counters since trg_create: out[0] subspace iterations,
  * out[1] Rayleigh-Ritz solves, out[2] FP32 Jacobi sweeps, out[3] FP64
  * Jacobi sweeps, out[4] Cholesky-QR column repairs, out[5] second
- * Cholesky-QR passes left out between power steps; n <= 8 entries. */
+ * Cholesky-QR passes left out between power steps, out[6] product shapes
+ * whose launch choice this context timed (autotune); n <= 8 entries. */
 int trg_get_counters(const trg_ctx* ctx, uint64_t* out, int n);
 
 /* ------------------------------------------------------------ misc ----- */

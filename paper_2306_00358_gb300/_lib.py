@@ -43,6 +43,7 @@ class trg_config(ctypes.Structure):
         ("fused_slices", c_int),
         ("fp64_max_dd", c_int),
         ("env_slices", c_int),
+        ("autotune", c_int),
     ]
 
 

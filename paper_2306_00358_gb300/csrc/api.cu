@@ -284,6 +284,7 @@ int trg_config_default(trg_config* cfg) {
     cfg->mma_pairs = 1;
     cfg->fused_slices = 1;
     cfg->env_slices = 0;
+    cfg->autotune = 1;
     return TRG_OK;
 }
 
@@ -291,6 +292,7 @@ static int validate_config(const trg_config& c) {
     if (c.precision != TRG_FP64 && c.precision != TRG_SPLIT_BF16) return TRG_EINVAL;
     if (c.split_slices < 2 || c.split_slices > 5) return TRG_EINVAL;
     if (c.env_slices != 0 && (c.env_slices < 2 || c.env_slices > 5)) return TRG_EINVAL;
+    if (c.autotune != 0 && c.autotune != 1) return TRG_EINVAL;
     if (c.split_from_step < 0 || c.fp64_max_dd < 0) return TRG_EINVAL;
     if (c.mma_pairs != 0 && c.mma_pairs != 1) return TRG_EINVAL;
     if (c.fused_slices < 0 || c.fused_slices > 2) return TRG_EINVAL;

@@ -49,7 +49,10 @@
 
 #include <algorithm>
 #include <cstring>
+#include <map>
 #include <mutex>
+#include <tuple>
+#include <vector>
 
 #include "internal.h"
 
@@ -1180,7 +1183,7 @@ void launch_mma_k(Ctx& ctx, const CUtensorMap& ta, const CUtensorMap& tb, const 
     const int tiles_m = (a.M + BM * CG - 1) / (BM * CG), tiles_n = (a.N + BN - 1) / BN;
     const int tiles = tiles_m * tiles_n;
     const int ctas = CG == 1 ? std::max(1, std::min(tiles, ctx.sm_count)) : 2 * std::max(1, std::min(tiles, max_clusters));
-    a.group_n = choose_group_n(tiles_m * CG, tiles_n, ctas, a.Kp, S);
+    if (a.group_n <= 0) a.group_n = choose_group_n(tiles_m * CG, tiles_n, ctas, a.Kp, S);
     cudaError_t e;
     if (CG == 1) {
         const int grid = ctas;
@@ -1277,6 +1280,72 @@ int64_t split_rows_padded(const Ctx& ctx, int64_t M) {
 }
 int64_t split_k_padded(int64_t K) { return (std::max<int64_t>(K, 1) + BK - 1) / BK * BK; }
 
+// Measured launch choice of a split product (the tile autotuner): one CTA or
+// a CTA pair per tile, and the width of the tile groups (tile_coords).  Every
+// choice gives identical bits (the pair issues the same product table, and
+// the tile order changes no sum), so the choice is a pure speed decision and
+// results never depend on it.  On the first product of a shape (M, N, K, S,
+// epilogue kind) worth tuning, each candidate is launched twice and timed
+// with events on the context's stream; the fastest is kept in a table shared
+// by every context of the process.  Smaller products, and contexts with
+// autotune off, take the model choice (pairs as configured, choose_group_n).
+struct TuneChoice { int cg, group_n; };
+struct TuneKey {
+    int M, N, Kp, S, mode, cg_max;
+    bool operator<(const TuneKey& o) const {
+        return std::tie(M, N, Kp, S, mode, cg_max) < std::tie(o.M, o.N, o.Kp, o.S, o.mode, o.cg_max);
+    }
+};
+static std::mutex g_tune_mu;
+static std::map<TuneKey, TuneChoice> g_tune;
+constexpr double TUNE_MIN_MACS = 1.0 * (1 << 30);   // products below ~1 G multiply-adds keep the model choice
+
+template <class Launch>
+static TuneChoice tuned_choice(Ctx& ctx, int M, int N, int Kp, int S, int mode, int cg_max, Launch&& launch) {
+    const int tiles_n = (N + BN - 1) / BN;
+    auto model_group = [&](int cg) {
+        const int tiles_m = (M + BM * cg - 1) / (BM * cg);
+        const int ctas = std::max(1, std::min(tiles_m * tiles_n * cg, ctx.sm_count & ~(cg - 1)));
+        return choose_group_n(tiles_m * cg, tiles_n, ctas, Kp, S);
+    };
+    const TuneChoice model{cg_max, model_group(cg_max)};
+    if (!ctx.cfg.autotune || (double)M * N * Kp < TUNE_MIN_MACS) return model;
+    const TuneKey key{M, N, Kp, S, mode, cg_max};
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        auto it = g_tune.find(key);
+        if (it != g_tune.end()) return it->second;
+    }
+    std::vector<TuneChoice> cand;
+    for (int cg = cg_max; cg >= 1; --cg) {
+        const int g = model_group(cg);
+        for (int gn : {g, std::max(1, g / 2), std::min(tiles_n, 2 * g)}) {
+            bool seen = false;
+            for (auto& c : cand) seen = seen || (c.cg == cg && c.group_n == gn);
+            if (!seen) cand.push_back({cg, gn});
+        }
+    }
+    cudaEvent_t e0 = ctx.get_event(), e1 = ctx.get_event();
+    TuneChoice best = model;
+    float best_ms = 1e30f;
+    for (const TuneChoice& c : cand) {
+        launch(c.cg, c.group_n);     // warm (the output is the same every time)
+        TRG_CUDA(cudaEventRecord(e0, ctx.stream));
+        launch(c.cg, c.group_n);
+        TRG_CUDA(cudaEventRecord(e1, ctx.stream));
+        TRG_CUDA(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        TRG_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+        if (ms < best_ms) { best_ms = ms; best = c; }
+    }
+    ctx.event_pool.push_back(e0);
+    ctx.event_pool.push_back(e1);
+    ctx.counters[6] += 1;
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    g_tune.emplace(key, best);
+    return g_tune[key];
+}
+
 void gemm_split(Ctx& ctx, const GemmDesc& d) {
     if (d.M <= 0 || d.N <= 0) return;
     if (d.beta != 0.0) fail(TRG_EINVAL, "split GEMM overwrites its output (beta must be 0)");
@@ -1350,18 +1419,24 @@ void gemm_split(Ctx& ctx, const GemmDesc& d) {
                               d.cons_m && d.cons_n && d.ck_m && d.ck_n && d.cs_e;
         if (!shape_ok) fail(TRG_EINVAL, "fused slice hand-over: consumer rows do not tile");
     }
+    auto launch = [&](int cg, int group_n) {
+        MmaArgs b = a;
+        b.group_n = group_n;
+        switch (S * 2 + cg - 1) {
+            case 4: launch_mma<2, 1>(ctx, ta, tb, tbh, b); break;
+            case 5: launch_mma<2, 2>(ctx, ta, tb, tbh, b); break;
+            case 6: launch_mma<3, 1>(ctx, ta, tb, tbh, b); break;
+            case 7: launch_mma<3, 2>(ctx, ta, tb, tbh, b); break;
+            case 8: launch_mma<4, 1>(ctx, ta, tb, tbh, b); break;
+            case 9: launch_mma<4, 2>(ctx, ta, tb, tbh, b); break;
+            case 10: launch_mma<5, 1>(ctx, ta, tb, tbh, b); break;
+            case 11: launch_mma<5, 2>(ctx, ta, tb, tbh, b); break;
+        }
+    };
+    const TuneChoice ch = tuned_choice(ctx, M, N, Kp, S, d.cs_out ? 2 : (d.c_rows_fast ? 1 : 0), CG, launch);
     const int tok = ctx.region_begin(TRG_PHASE_MMA);
     const int tok_x2 = ctx.phase == TRG_PHASE_X2 ? ctx.region_begin(TRG_PHASE_MMA_X2) : -1;
-    switch (S * 2 + CG - 1) {
-        case 4: launch_mma<2, 1>(ctx, ta, tb, tbh, a); break;
-        case 5: launch_mma<2, 2>(ctx, ta, tb, tbh, a); break;
-        case 6: launch_mma<3, 1>(ctx, ta, tb, tbh, a); break;
-        case 7: launch_mma<3, 2>(ctx, ta, tb, tbh, a); break;
-        case 8: launch_mma<4, 1>(ctx, ta, tb, tbh, a); break;
-        case 9: launch_mma<4, 2>(ctx, ta, tb, tbh, a); break;
-        case 10: launch_mma<5, 1>(ctx, ta, tb, tbh, a); break;
-        case 11: launch_mma<5, 2>(ctx, ta, tb, tbh, a); break;
-    }
+    launch(ch.cg, ch.group_n);
     const double products = (double)S * (S + 1) / 2;
     ctx.region_end(tok_x2, 2.0 * (double)M * N * K, products * 2.0 * (double)M * N * Kp);
     ctx.region_end(tok, 2.0 * (double)M * N * K, products * 2.0 * (double)M * N * Kp);

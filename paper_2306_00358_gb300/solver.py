@@ -210,10 +210,10 @@ class Solver:
         return int(self._lib.trg_launch_count(self._h))
 
     def counters(self) -> dict:
-        arr = (_lib.c_uint64 * 6)()
-        self._check(self._lib.trg_get_counters(self._h, arr, 6), "trg_get_counters")
+        arr = (_lib.c_uint64 * 7)()
+        self._check(self._lib.trg_get_counters(self._h, arr, 7), "trg_get_counters")
         names = ("subspace_iterations", "rayleigh_ritz", "jacobi_sweeps_fp32", "jacobi_sweeps_fp64",
-                 "cholqr_repairs", "cholqr_single_pass")
+                 "cholqr_repairs", "cholqr_single_pass", "shapes_tuned")
         return {k: int(v) for k, v in zip(names, arr)}
 
     def profile(self, on: bool = True):
