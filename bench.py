@@ -218,7 +218,8 @@ def load_peaks():
 # kernel in this workload (the profiles directory holds its summary).  The
 # figure describes the kernel source it was taken on: reported only while
 # that file is unchanged, else null.
-SPLIT_MMA_TRAFFIC = {"sha256": None, "bytes_per_launch": None}
+SPLIT_MMA_TRAFFIC = {"sha256": "bf02ec2c32f1ef3fd38722b41db2483727fb6cf51541e3ed8ecb95d17791f54c",
+                     "bytes_per_launch": 1.4699e10}
 # Algorithmic bytes of one X2 launch at Dcut 64, S = 4: read the A slices
 # (S x 65536 x 4096 BF16) and the B slices (S x 4096 x 4096 BF16), write the
 # next product's A slices (S x 65536 x 4096 BF16) and row exponents.
