@@ -45,6 +45,8 @@ def parse():
     ap.add_argument("--no-accuracy", action="store_true",
                     help="skip the headline accuracy leg (split and FP64 solves of the Dcut-64 beta_c workload)")
     ap.add_argument("--no-calibration", action="store_true", help="skip the in-run calibration products")
+    ap.add_argument("--no-serve-sample", action="store_true",
+                    help="skip the short serving leg (p50/p99 latency and solves/s of a sample of the serving mix)")
     ap.add_argument("--workspace-bytes", type=int, default=0,
                     help="bound of the contraction workspace (0 = the library default, 4 GiB: 16 values of j "
                          "per D^7 launch at Dcut 64)")
@@ -52,6 +54,9 @@ def parse():
                     help="slice hand-over between contraction products: none (0), D^7 -> last (1), all (2)")
     ap.add_argument("--mma-pairs", type=int, default=1, choices=[0, 1],
                     help="split products on CTA pairs (1) or one CTA per tile (0)")
+    ap.add_argument("--shard", action="store_true",
+                    help="under torchrun: one solve split over the ranks (the contraction's rows of j per rank, "
+                         "one all-gather per half-step; strong scaling) instead of one solve per rank")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-solve", action="store_true", help="skip timing one full 40-half-step solve")
@@ -145,37 +150,54 @@ class ClockSampler:
 
 
 # ----------------------------------------------------------- CPU baseline ---
+_JACOBI_GROWTH = {}
+
+
 def oracle_half_step_sample():
     """Time the oracle on a bounded sample of one D=64 half-step and scale it
-    to the whole half-step.  Returns (seconds per half-step, description)."""
+    to the whole half-step.  Returns (seconds per half-step, description).
+
+    * contraction: the oracle's j-slice contraction for one of the 64 values
+      of j and 8 of the 64 kept columns of U (its cost, the D^7 product X2
+      first, is linear in both), times 64 x 8;
+    * environment: in full;
+    * eigensolve: the oracle's cyclic Jacobi (one core) on a 256 x 256 graded
+      PSD block, carried to n = 4096 by the growth measured once per process
+      between 256 and 512 (not an assumed n^3)."""
+    import numpy as np
+
     from oracle import hotrg, jacobi
     from paper_2306_00358_gb300 import workloads
 
-    d = DCUT
+    d, ncols = DCUT, 8
     t = workloads.random_tensor((d, d, d, d), seed=11) * 1e-2
     u = workloads.random_isometry(d, d, seed=12)
-    # contraction: one j-slice of 64 (the slices are identical in cost)
     t0 = time.perf_counter()
-    hotrg.contract_x_slice(t, u, 0, 1)
-    t_con = (time.perf_counter() - t0) * d
+    hotrg.contract_x_slice(t, np.ascontiguousarray(u[:, :, :ncols]), 0, 1)
+    t_con = (time.perf_counter() - t0) * d * (d // ncols)
     t0 = time.perf_counter()
     hotrg.environment_x(t)
     t_env = time.perf_counter() - t0
-    # eigensolve: the oracle's cyclic Jacobi (one core) on 256 x 256 and 512 x
-    # 512 graded PSD blocks; the measured growth between the two sizes (not an
-    # assumed n^3) carries the 512 time to n = 4096
-    times = {}
-    for nb in (256, 512):
-        m = workloads.graded_psd(nb, 16, seed=13)
-        t0 = time.perf_counter()
-        jacobi.eigh(m)
-        times[nb] = time.perf_counter() - t0
-    expo = math.log(times[512] / times[256]) / math.log(2.0)
-    t_eig = times[512] * (d * d / 512) ** expo
+    if "expo" not in _JACOBI_GROWTH:
+        times = {}
+        for nb in (256, 512):
+            m = workloads.graded_psd(nb, 16, seed=13)
+            t0 = time.perf_counter()
+            jacobi.eigh(m)
+            times[nb] = time.perf_counter() - t0
+        _JACOBI_GROWTH["expo"] = math.log(times[512] / times[256]) / math.log(2.0)
+        _JACOBI_GROWTH["t512"] = times[512]
+    expo = _JACOBI_GROWTH["expo"]
+    m = workloads.graded_psd(256, 16, seed=13)
+    t0 = time.perf_counter()
+    jacobi.eigh(m)
+    t256 = time.perf_counter() - t0
+    t_eig = t256 * (d * d / 256) ** expo
     total = t_con + t_env + t_eig
-    desc = (f"oracle at D=64: contraction 1 of 64 j-slices x64 ({t_con:.1f}s, numpy on all cores), environment "
-            f"in full ({t_env:.1f}s), cyclic Jacobi on one core: 256^2 {times[256]:.2f}s, 512^2 {times[512]:.2f}s, "
-            f"growth n^{expo:.2f} carried to 4096^2 ({t_eig:.0f}s)")
+    desc = (f"oracle at D=64: contraction of 1 of 64 j-slices with 8 of 64 kept columns x512 ({t_con:.1f}s, numpy "
+            f"on all cores), environment in full ({t_env:.1f}s), cyclic Jacobi on one core at 256^2 ({t256:.2f}s) "
+            f"carried to 4096^2 by the growth n^{expo:.2f} measured between 256^2 and 512^2 "
+            f"({_JACOBI_GROWTH['t512']:.2f}s) ({t_eig:.0f}s)")
     return total, desc
 
 
@@ -384,10 +406,15 @@ def run_native(args):
         extra["workspace_bytes"] = args.workspace_bytes
     s = Solver(local, stream=stream, precision=precision, split_slices=args.slices, mma_pairs=args.mma_pairs,
                fused_slices=args.fused_slices, **extra)
-    beta = replica_beta(rank)
+    shard = args.shard and world > 1
+    beta = BETA_C if shard else replica_beta(rank)
     s.init_tensor("ising", beta, 0.0)
     s.coarse_grain(DCUT, STEADY_AT)
-    s.coarse_grain(DCUT, warmup)
+    stepper = s
+    if shard:
+        from paper_2306_00358_gb300.sharding import ShardedSolver
+        stepper = ShardedSolver(s, device=torch.device("cuda", local))
+    stepper.coarse_grain(DCUT, warmup)
     barrier()
     s.profile(True)
     launches0 = s.launch_count()
@@ -399,7 +426,7 @@ def run_native(args):
     barrier()
     torch.cuda.nvtx.range_push("timed")      # lets a profiler select the timed launches
     ev0.record(stream)
-    s.coarse_grain(DCUT, steps)
+    stepper.coarse_grain(DCUT, steps)
     ev1.record(stream)
     torch.cuda.nvtx.range_pop()
     barrier()
@@ -410,7 +437,8 @@ def run_native(args):
     ph = s.phase_stats()
     s.profile(False)
     ms_max = max_over_ranks(ms, world)
-    sec_per_step = seconds_per_half_step(ms_max, steps, world)
+    # replicas: every rank's half-steps count; one split solve: its own only
+    sec_per_step = seconds_per_half_step(ms_max, steps, 1 if shard else world)
 
     # roofline of the dominant kernel: the D^7 product
     peaks = load_peaks()
@@ -462,7 +490,7 @@ def run_native(args):
         ne = max(1, min(steps, 3))
         for _ in range(ne):
             s2.init_tensor_raw(t_host, beta)       # host -> device copy of the step's input
-            s2.coarse_grain(DCUT, 1)
+            (stepper if shard else s2).coarse_grain(DCUT, 1)
             f, _ = s2.free_energy()                # device -> host read of the result
         torch.cuda.synchronize()
         e2e_s = (time.perf_counter() - t0) / ne
@@ -485,6 +513,9 @@ def run_native(args):
     acc = None
     if rank == 0 and world == 1 and not args.no_accuracy and precision == "split":
         acc = accuracy_leg(args.slices, args.env_slices)
+    serve = None
+    if rank == 0 and world == 1 and not args.no_serve_sample and precision == "split":
+        serve = serve_sample(args.slices)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -493,18 +524,21 @@ def run_native(args):
 
     if rank == 0:
         line = {"metric": METRIC, "value": sec_per_step, "unit": "s/half-step", "n_gpus": world, "steps": steps,
-                "warmup": warmup, "ms_per_step": ms_max / steps, "higher_is_better": False, "scaling": "weak",
+                "warmup": warmup, "ms_per_step": ms_max / steps, "higher_is_better": False,
+                "scaling": "strong" if shard else "weak",
                 "vs_baseline": None, "dtype": "f64" if precision == "fp64" else "bf16-slices(x%d)->f64" % args.slices,
                 "data": "synthetic",
                 "config": {"workload": WORKLOAD, "precision": precision, "dcut": DCUT,
                            "l2": "inputs larger than L2 (T 134 MB, M 134 MB, workspace >= 1 GB per step)",
-                           "parallelism": "replicas" if world > 1 else "single"},
+                           "parallelism": ("j-sharded solve" if shard else "replicas") if world > 1 else "single"},
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
                 "phases_ms": {k: round(v["ms"], 3) for k, v in ph.items()}, "counters": counters, "solve": solve,
-                "calibration": calib, "accuracy": acc}
+                "calibration": calib, "accuracy": acc, "serve_sample": serve}
         if acc:
             line.update({"f_split": acc["f_split"], "f_fp64": acc["f_fp64"], "abs_df": acc["abs_df"],
                          "fp64_s_per_step": acc["fp64_s_per_step"]})
+        if serve:
+            line.update({"p99_serve_latency_s": serve["p99_latency_s"], "serve_solves_per_s": serve["solves_per_s"]})
         print(json.dumps(line), flush=True)
     s.close()
     if world > 1:
@@ -655,25 +689,61 @@ def run_batch(args):
                       "dcut_counts": counts, "speedup_vs_serial_fp64": serial / wall}), flush=True)
 
 
-def run_serve(args):
-    """Serving: a Poisson stream of requests (config 5 mix) into the solve
-    engine; reports p50/p99 latency and solves/s."""
+def serve_mix(n, seed, slices):
+    """n requests of the serving mix (config 5): Ising:XY 0.7:0.3, beta
+    uniform in [0.35, 0.55] / [0.8, 1.3], h in {0, 1e-3, 1e-2}, Dcut in
+    {16, 24, 32, 48, 64, 96} weighted .3/.25/.2/.15/.07/.03, 20-40 half-steps."""
     import numpy as np
 
     from paper_2306_00358_gb300 import serving as sv
-    rng = np.random.default_rng(args.seed)
+    rng = np.random.default_rng(seed)
     dcuts = [16, 24, 32, 48, 64, 96]
     weights = [0.30, 0.25, 0.20, 0.15, 0.07, 0.03]
     specs = []
-    for _ in range(args.requests):
+    for _ in range(n):
         if rng.random() < 0.7:
             model, beta = "ising", float(rng.uniform(0.35, 0.55))
         else:
             model, beta = "xy", float(rng.uniform(0.8, 1.3))
         specs.append(sv.Spec(model=model, beta=beta, h=float(rng.choice([0.0, 1e-3, 1e-2])),
                              dcut=int(rng.choice(dcuts, p=weights)), nsteps=int(rng.integers(20, 41)),
-                             precision="split", slices=args.slices,
+                             precision="split", slices=slices,
                              trunc="multiplet" if model == "xy" else "paper"))
+    return specs, rng
+
+
+def serve_sample(slices, n=32, rate=0.6, seed=4321):
+    """A short serving run for the bench line: n requests of the serving mix
+    arriving as a Poisson stream at `rate` per second, 16 slots, 150 GB
+    budget; p50/p99 latency (submit -> result) and solves/s."""
+    import numpy as np
+
+    from paper_2306_00358_gb300 import serving as sv
+    specs, rng = serve_mix(n, seed, slices)
+    gaps = rng.exponential(1.0 / rate, size=len(specs))
+    with sv.Server(0, slots=16, hbm_budget_bytes=150 << 30, workspace_bytes=1 << 30) as s:
+        t0 = time.perf_counter()
+        tickets = []
+        for spec, gap in zip(specs, gaps):
+            time.sleep(gap)
+            tickets.append(s.submit(spec))
+        res = [s.wait(t) for t in tickets]
+        wall = time.perf_counter() - t0
+        st = s.stats()
+    lat = np.array([r["seconds_queued"] + r["seconds_run"] for r in res])
+    return {"requests": n, "rate_per_s": rate, "seed": seed, "ok": sum(r["status"] == 0 for r in res),
+            "wall_s": wall, "p50_latency_s": float(np.percentile(lat, 50)),
+            "p99_latency_s": float(np.percentile(lat, 99)), "solves_per_s": st["solves_per_s"],
+            "dcuts": sorted(int(s.dcut) for s in specs)}
+
+
+def run_serve(args):
+    """Serving: a Poisson stream of requests (config 5 mix) into the solve
+    engine; reports p50/p99 latency and solves/s."""
+    import numpy as np
+
+    from paper_2306_00358_gb300 import serving as sv
+    specs, rng = serve_mix(args.requests, args.seed, args.slices)
     gaps = rng.exponential(1.0 / args.rate, size=len(specs))
     with sv.Server(0, slots=args.slots, hbm_budget_bytes=150 << 30, workspace_bytes=1 << 30,
                    policy=args.policy) as s:

@@ -98,16 +98,22 @@ DCUT32_CASES = [
 ]
 
 
+# The truncated XY model (D0 = 9, charges |n| <= 4) at Dcut 32, 30 half-steps
+# (the lattice of the XY runs), multiplet truncation: the oracle's 1024 x 1024
+# Jacobi solves make each of these tens of CPU-minutes too.
+XY32_CASES = [(f"xy_b{b:g}_d32_n30", "xy", b, 0.0, 32, 30, "multiplet") for b in (1.0, 1.1)]
+
+
 def _run_case(case):
     return case[0], run(*case)
 
 
-def dcut32(names=None):
+def dcut32(names=None, cases_all=None, fname="oracle_solves_dcut32.json"):
     """oracle_solves_dcut32.json: the Dcut-32 coupling grid (or the named
     subset of it), one process per solve."""
     import multiprocessing as mp
-    cases = [c for c in DCUT32_CASES if not names or c[0] in names]
-    path = os.path.join(HERE, "oracle_solves_dcut32.json")
+    cases = [c for c in (cases_all or DCUT32_CASES) if not names or c[0] in names]
+    path = os.path.join(HERE, fname)
     out = json.load(open(path)) if os.path.exists(path) else {}
     with mp.get_context("spawn").Pool(len(cases)) as pool:
         for name, rec in pool.imap_unordered(_run_case, cases):
@@ -115,7 +121,7 @@ def dcut32(names=None):
             out[name] = rec
             with open(path, "w") as fh:
                 json.dump(dict(sorted(out.items())), fh, indent=1)
-    print("wrote oracle_solves_dcut32.json")
+    print("wrote", fname)
 
 
 def main():
@@ -124,6 +130,9 @@ def main():
         return
     if "--dcut32" in sys.argv:
         dcut32([a for a in sys.argv[1:] if not a.startswith("--")])
+        return
+    if "--xy32" in sys.argv:
+        dcut32([a for a in sys.argv[1:] if not a.startswith("--")], XY32_CASES, "oracle_solves_xy32.json")
         return
     expectations()
     out = {}

@@ -52,6 +52,9 @@ def test_status_strings_and_defaults():
     assert cfg.split_slices == 4
     assert cfg.oversample == 24
     assert cfg.eig_tol == 1e-12
+    # the fields after the first ones land where the C struct has them
+    assert (cfg.mma_pairs, cfg.fused_slices, cfg.fp64_max_dd, cfg.env_slices, cfg.autotune) == (1, 1, 16, 0, 1)
+    assert cfg.split_from_step == 0 and cfg.workspace_bytes == 0
     assert lib.trg_config_default(None) == _lib.TRG_EINVAL
 
 

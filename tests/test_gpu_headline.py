@@ -11,6 +11,10 @@ dimensions 32, 48 and 64.
   GPU path on the same solve, |f_split - f_fp64| <= 1e-9; the FP64 path is
   itself pinned to the oracle at Dcut <= 32.  The Dcut-64 FP64 solve takes
   about four and a half minutes (marked slow).
+* XY model (the O(2) case of Sec. 3.3, multiplet-preserving cuts) at
+  beta 1.0 and 1.1, Dcut 32, 30 half-steps: the GPU against the oracle
+  (tests/golden/oracle_solves_xy32.json, make_golden.py --xy32), the same
+  bounds as the Ising grid.
 """
 import json
 import math
@@ -24,6 +28,7 @@ from paper_2306_00358_gb300 import Solver
 pytestmark = pytest.mark.gpu
 HERE = os.path.dirname(os.path.abspath(__file__))
 GOLDEN32 = json.load(open(os.path.join(HERE, "golden", "oracle_solves_dcut32.json")))
+GOLDEN_XY32 = json.load(open(os.path.join(HERE, "golden", "oracle_solves_xy32.json")))
 BETA_C = 0.5 * math.log(1.0 + math.sqrt(2.0))
 
 F_TOL_FP64 = 1e-10
@@ -57,11 +62,15 @@ def test_dcut32_golden_covers_the_grid():
         assert g["dcut"] == 32 and g["nsteps"] == 40 and g["model"] == "ising"
 
 
-@pytest.mark.parametrize("name", sorted(GOLDEN32))
-def test_dcut32_fp64_matches_oracle(torch, name):
-    g = GOLDEN32[name]
-    f, spectra, dims = _solve("ising", g["beta"], g["h"], 32, 40, spectra=True, precision="fp64",
-                              trunc=g["trunc"], eig_tol=1e-13)
+def test_xy32_golden_covers_two_couplings():
+    assert sorted(g["beta"] for g in GOLDEN_XY32.values()) == [1.0, 1.1]
+    for g in GOLDEN_XY32.values():
+        assert g["model"] == "xy" and g["dcut"] == 32 and g["trunc"] == "multiplet"
+
+
+def _fp64_against(g):
+    f, spectra, dims = _solve(g["model"], g["beta"], g["h"], g["dcut"], g["nsteps"], spectra=True,
+                              precision="fp64", trunc=g["trunc"], eig_tol=1e-13)
     assert dims == g["steps"][-1]["dims"]
     assert abs(f - g["f"]) <= F_TOL_FP64, (f, g["f"])
     compared = 0
@@ -82,12 +91,30 @@ def test_dcut32_fp64_matches_oracle(torch, name):
     assert compared >= 1
 
 
-@pytest.mark.parametrize("name", sorted(GOLDEN32))
-def test_dcut32_split_matches_oracle(torch, name):
-    g = GOLDEN32[name]
-    f, _, dims = _solve("ising", g["beta"], g["h"], 32, 40, trunc=g["trunc"], **SPLIT)
+def _split_against(g):
+    f, _, dims = _solve(g["model"], g["beta"], g["h"], g["dcut"], g["nsteps"], trunc=g["trunc"], **SPLIT)
     assert dims == g["steps"][-1]["dims"]
     assert abs(f - g["f"]) <= F_TOL_SPLIT, (f, g["f"])
+
+
+@pytest.mark.parametrize("name", sorted(GOLDEN32))
+def test_dcut32_fp64_matches_oracle(torch, name):
+    _fp64_against(GOLDEN32[name])
+
+
+@pytest.mark.parametrize("name", sorted(GOLDEN32))
+def test_dcut32_split_matches_oracle(torch, name):
+    _split_against(GOLDEN32[name])
+
+
+@pytest.mark.parametrize("name", sorted(GOLDEN_XY32))
+def test_xy32_fp64_matches_oracle(torch, name):
+    _fp64_against(GOLDEN_XY32[name])
+
+
+@pytest.mark.parametrize("name", sorted(GOLDEN_XY32))
+def test_xy32_split_matches_oracle(torch, name):
+    _split_against(GOLDEN_XY32[name])
 
 
 @pytest.mark.slow
