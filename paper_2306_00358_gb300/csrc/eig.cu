@@ -260,13 +260,18 @@ __global__ void __launch_bounds__(64) k_gram_reduce(const double* part, int npar
 // column-major).  Rotation (p,q): tau = (h_qq - h_pp)/(2 h_pq),
 // t = sign(tau)/(|tau| + sqrt(1+tau^2)), c = 1/sqrt(1+t^2), s = t c;
 // H <- J^T H J.  Rotations with |h_pq| <= tol sqrt(|h_pp h_qq|) are skipped
-// (relative-accuracy threshold for graded matrices); a sweep without
-// rotations ends the loop.  Returns the number of sweeps (max_sweeps + 1 if
-// the limit was hit).  All threads of the block call it.
+// (relative-accuracy threshold for graded matrices); the loop ends when no
+// pair is above the threshold.  Returns the number of sweeps that rotated
+// (max_sweeps + 1 if the limit was hit).  All threads of the block call it.
 __device__ __forceinline__ void rr_pair(int r, int i, int mp, int& p, int& q) {
     if (i == 0) { p = mp - 1; q = r; }
     else { p = (r + i) % (mp - 1); q = (r - i + (mp - 1)) % (mp - 1); }
     if (p > q) { const int x = p; p = q; q = x; }
+}
+
+template <typename T>
+__device__ __forceinline__ bool jacobi_rotates(T hpq, T hpp, T hqq, T tol) {
+    return fabs(hpq) > tol * sqrt(fabs(hpp * hqq)) && fabs(hpq) > (T)1e-300;
 }
 
 template <typename T>
@@ -275,7 +280,17 @@ __device__ int jacobi_sweeps(T* H, int ld, T* W, int m, T tol, int max_sweeps, T
     const int npair = mp / 2;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
     for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+        // A sweep rotates nothing exactly when no pair of the current H is
+        // above the threshold (H only changes by rotations), so one scan of
+        // the pairs stands in for that last, confirming sweep.
         if (threadIdx.x == 0) *rot = 0;
+        __syncthreads();
+        for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
+            const int p = e / m, q = e % m;
+            if (p < q && jacobi_rotates<T>(H[p * ld + q], H[p * ld + p], H[q * ld + q], tol)) *(volatile int*)rot = 1;
+        }
+        __syncthreads();
+        if (*rot == 0) return sweep;
         __syncthreads();
         for (int r = 0; r < mp - 1; ++r) {
             for (int i = threadIdx.x; i < npair; i += blockDim.x) {
@@ -284,12 +299,11 @@ __device__ int jacobi_sweeps(T* H, int ld, T* W, int m, T tol, int max_sweeps, T
                 T c = 1, s = 0;
                 if (q < m) {
                     const T hpq = H[p * ld + q], hpp = H[p * ld + p], hqq = H[q * ld + q];
-                    if (fabs(hpq) > tol * sqrt(fabs(hpp * hqq)) && fabs(hpq) > (T)1e-300) {
+                    if (jacobi_rotates<T>(hpq, hpp, hqq, tol)) {
                         const T tau = (hqq - hpp) / (2 * hpq);
                         const T t = (tau >= 0) ? 1 / (tau + sqrt(1 + tau * tau)) : -1 / (-tau + sqrt(1 + tau * tau));
                         c = 1 / sqrt(1 + t * t);
                         s = t * c;
-                        atomicAdd(rot, 1);
                     }
                 }
                 cs[2 * i] = c;
@@ -334,9 +348,6 @@ __device__ int jacobi_sweeps(T* H, int ld, T* W, int m, T tol, int max_sweeps, T
             }
             __syncthreads();
         }
-        const int nrot = *rot;
-        __syncthreads();
-        if (nrot == 0) return sweep + 1;
     }
     return max_sweeps + 1;
 }
@@ -346,13 +357,16 @@ __device__ int jacobi_sweeps(T* H, int ld, T* W, int m, T tol, int max_sweeps, T
 //  1. FP32 Jacobi on H / max|H| to a relative threshold of 1e-6 (the FP32
 //     pipe is ~60x the FP64 pipe on this part); rotations accumulate in W32
 //     (k_rr_fp32, one CTA);
-//  2. W = W32 in FP64, re-orthonormalised by Cholesky-QR (W^T W = L L^T,
-//     W <- W L^-T), and H' = W^T H W formed in FP64: m x m products on many
-//     SMs (k_small_tn, k_small_nn), the Cholesky and the triangular solve of
-//     the Cholesky-QR path (k_chol_flag, k_trsm_rows);
-//  3. FP64 Jacobi sweeps on H' (it starts ~1e-6 off diagonal, so one
-//     quadratically convergent sweep and a confirming one finish it),
-//     W <- W J (k_rr_fp64, one CTA).
+//  2. W = W32 in FP64, refined by two Ogita-Aishima steps and a Lowdin
+//     step (k_oa_step, k_lowdin): m x m FP64 products on many SMs
+//     (k_small_nn, k_small_tn, k_small_apply) that leave W orthonormal to
+//     rounding and the couplings of the separated pairs of H' = W^T H W
+//     squared twice (at beta_c, Dcut 24, none is left above the FP64
+//     threshold; off critical a graded tail of a few hundred pairs is);
+//  3. FP64 Jacobi sweeps on H' (k_rr_fp64, one CTA): they find only the
+//     pairs step 2 left coupled (near-degenerate ones), W <- W J.
+// A rough Rayleigh-Ritz far from convergence (no FP64 sweeps) instead
+// re-orthonormalises W32 by Cholesky-QR and takes theta = diag(W^T H W).
 // Output: theta sorted descending, W (column-major, global) in that order.
 // Shared memory of the one-CTA kernels: H (m rows of ld = m + 1 doubles: the
 // odd stride puts the rows of one column in different banks, so the column
@@ -414,11 +428,75 @@ __global__ void __launch_bounds__(128) k_small_nn(const double* H, const double*
     }
 }
 
-// Step 3 of the Rayleigh-Ritz solve: H = (G + G^T) / 2, FP64 sweeps from W,
-// then theta and W sorted by descending theta (ties keep index order).
+// Xout = X (I + E) = X + X E for a column-major m x m X and a row-major E:
+// a CTA per column j, a thread per row r, the sum in order of k.
+__global__ void __launch_bounds__(128) k_small_apply(const double* X, const double* E, int m, double* Xout) {
+    const int j = blockIdx.x;
+    for (int r = threadIdx.x; r < m; r += blockDim.x) {
+        double a = 0.0;
+        for (int k = 0; k < m; ++k) a = fma(X[(int64_t)k * m + r], E[(int64_t)k * m + j], a);
+        Xout[(int64_t)j * m + r] = X[(int64_t)j * m + r] + a;
+    }
+}
+
+// One refinement step of an approximate eigenbasis X of the symmetric H
+// after Ogita and Aishima (Iterative refinement for symmetric eigenvalue
+// decomposition, Japan J. Indust. Appl. Math. 35, 2018).  With S = X^T H X
+// (symmetrised here) and P = X^T X = I - R:
+//   lambda_i = s_ii / p_ii,
+//   E_ij = (s_ij + lambda_j r_ij) / (lambda_j - lambda_i)   for a separated pair,
+//   E_ij = r_ij / 2                                         otherwise and for i = j,
+// and X <- X (I + E) (k_small_apply): to first order that makes X^T X = I
+// (E + E^T = R) and zeroes the separated couplings, so both shrink
+// quadratically from step to step.  Where the published step separates
+// pairs by one global gap bound, this one takes a pair as separated when
+// |lambda_j - lambda_i| > OA_SEP (|s_ij| + max(|lambda_i|, |lambda_j|) |r_ij|),
+// i.e. |E_ij| < 1 / OA_SEP: a symmetric test, so E + E^T = R holds exactly,
+// and a strict one, so that the second-order terms (X^T X - I after a step
+// is about E^T E) stay small even where the FP32 vectors of a graded tail
+// are poor.  Pairs it leaves coupled (near-degenerate ones, the tail) are
+// left to FP64 Jacobi.
+// One CTA.
+constexpr double OA_SEP = 256.0;
+constexpr int OA_STEPS = 2;
+__global__ void __launch_bounds__(256) k_oa_step(const double* S, const double* P, int m, double* E) {
+    __shared__ double lam[MAX_M];
+    for (int i = threadIdx.x; i < m; i += blockDim.x) lam[i] = S[(int64_t)i * m + i] / P[(int64_t)i * m + i];
+    __syncthreads();
+    for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
+        const int i = e / m, j = e % m;
+        const double r = (i == j ? 1.0 : 0.0) - P[e];
+        double v = 0.5 * r;
+        if (i != j) {
+            const double sij = 0.5 * (S[e] + S[(int64_t)j * m + i]);
+            const double gap = lam[j] - lam[i];
+            const double bound = OA_SEP * (fabs(sij) + fmax(fabs(lam[i]), fabs(lam[j])) * fabs(r));
+            if (fabs(gap) > bound) v = (sij + lam[j] * r) / gap;
+        }
+        E[e] = v;
+    }
+}
+
+// Second-order Lowdin (symmetric) orthonormalisation: for X^T X = P = I - R
+// with R small, X (I + F) with F = R / 2 + 3 R^2 / 8 (the series of
+// (I - R)^(-1/2)) has (I + F)^T P (I + F) = I + O(R^3).  PP = P P gives
+// R^2 = PP - 2 P + I.  F is row-major (P, PP symmetric).
+__global__ void __launch_bounds__(256) k_lowdin(const double* P, const double* PP, int m, double* F) {
+    for (int e = threadIdx.x + blockIdx.x * blockDim.x; e < m * m; e += blockDim.x * gridDim.x) {
+        const int i = e / m, j = e % m;
+        const double id = (i == j) ? 1.0 : 0.0;
+        const double r = id - P[e];
+        const double r2 = PP[e] - 2.0 * P[e] + id;
+        F[e] = 0.5 * r + 0.375 * r2;
+    }
+}
+
+// Step 3 of the Rayleigh-Ritz solve: H = (G + G^T) / 2, FP64 sweeps from
+// W = Win (accumulated in shared memory), then theta and W sorted by
+// descending theta (ties keep index order) into Wout (may alias Win).
 __global__ void __launch_bounds__(512) k_rr_fp64(const double* G, int m, double tol, int max_sweeps,
-                                                 double* theta, double* Wout, int* status, int* sweeps_out,
-                                                 int fp64_sweeps) {
+                                                 double* theta, const double* Win, double* Wout, int* status,
+                                                 int* sweeps_out, int fp64_sweeps) {
     extern __shared__ double sm[];
     const int mp = m + (m & 1);
     const int ld = m + 1;
@@ -431,7 +509,7 @@ __global__ void __launch_bounds__(512) k_rr_fp64(const double* G, int m, double 
     for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
         const int i = e / m, j = e % m;
         H[i * ld + j] = 0.5 * (G[(int64_t)i * m + j] + G[(int64_t)j * m + i]);
-        Ws[e] = Wout[e];
+        Ws[e] = Win[e];
     }
     __syncthreads();
     // (skipped for a rough Rayleigh-Ritz far from convergence: then theta is
@@ -598,7 +676,7 @@ int isometry(Ctx& ctx, const double* M, int64_t n, int dcut, double* U, std::vec
     });
     // buffers: Q, Y, Z, QW (n x m each); G, L, W (m x m); theta (m)
     ctx.ensure(ctx.eig, (size_t)(4 * n * m) * sizeof(double));
-    ctx.ensure(ctx.eig_small, (size_t)(6 * m * m + 2 * m + 8) * sizeof(double));
+    ctx.ensure(ctx.eig_small, (size_t)(9 * m * m + 2 * m + 8) * sizeof(double));
     ctx.ensure(ctx.flags, (size_t)(m + 8) * sizeof(int));
     double* Q = ctx.eig.as<double>();
     double* Y = Q + n * m;
@@ -611,6 +689,9 @@ int isometry(Ctx& ctx, const double* M, int64_t n, int dcut, double* U, std::vec
     double* Hs = theta + 2 * m + 8;    // Rayleigh-Ritz scratch: symmetrised H, H W, Gram matrices
     double* T1 = Hs + m * m;
     double* G2 = T1 + m * m;
+    double* Pm = G2 + m * m;           // X^T X of the refinement
+    double* E = Pm + m * m;            // its correction
+    double* Xb = E + m * m;            // a second basis buffer
     int* flags = ctx.flags.as<int>();
     int* nbad = flags + m;
     int* sweeps = flags + m + 2;   // [0] FP32 sweeps, [1] FP64 sweeps of the last Rayleigh-Ritz
@@ -650,6 +731,7 @@ int isometry(Ctx& ctx, const double* M, int64_t n, int dcut, double* U, std::vec
         g.a_e = m_e;
         g.B.base = Q; g.B.off_r = ctx.table({{n, 1}}); g.B.off_c = ctx.table({{m, n}}); g.B.c_fast = false;
         g.C = Y; g.c_m = ctx.table({{n, 1}}); g.c_n = ctx.table({{m, n}}); g.beta = 0.0;
+        g.allow_ksplit = true;    // n / 128 tiles of 128 x m: K is split over the idle SMs
         gemm(ctx, g, precision);
     };
     // The number of products that reached the tolerance in the previous solve
@@ -709,29 +791,60 @@ int isometry(Ctx& ctx, const double* M, int64_t n, int dcut, double* U, std::vec
         // FP64 rotations stop at |h_pq| <= jtol sqrt(h_pp h_qq).  An unrotated
         // pair leaves at most m jtol theta_1 in a Ritz residual, so jtol =
         // 1e-3 tol keeps that far below the tolerance; with FP64 products
-        // (tol 1e-12) it is 1e-13: the FP32 sweeps leave ~1e-7, one
-        // quadratically convergent FP64 sweep ~1e-14, and the next sweep only
-        // confirms (eigenvalues exact to ~1e-26 relative, the vectors of pairs
-        // with a relative gap g to ~1e-13 / g).  With split products (tol
-        // 2^-(8S-10)) the first FP64 sweep already reaches jtol, which saves a
-        // whole sweep of rotations.
+        // (tol 1e-12) it is 1e-13 (eigenvalues exact to ~1e-26 relative, the
+        // vectors of pairs with a relative gap g to ~1e-13 / g), with split
+        // products (tol 2^-(8S-10)) 2.4e-10 at S = 4.
         const double jtol = std::max(1e-13, 1e-3 * tol);
         {
-            // the Rayleigh-Ritz solve of G = Q^T M Q into theta, W (see k_rr_fp32)
+            // the Rayleigh-Ritz solve of G = Q^T M Q into theta, W: FP32
+            // Jacobi, then (see k_rr_fp32) FP64 products and FP64 Jacobi
             k_rr_fp32<<<1, 512, rr32_smem(m), ctx.stream>>>(G, m, Hs, W, sweeps);
             TRG_LAUNCHED(ctx);
-            k_small_tn<<<m, 128, 0, ctx.stream>>>(W, W, m, G2);
-            TRG_LAUNCHED(ctx);
-            k_chol_flag<<<1, 256, chol_smem(m), ctx.stream>>>(G2, L, m, 0.0, flags, nbad, nullptr);
-            TRG_LAUNCHED(ctx);
-            k_trsm_rows<<<(unsigned)((m + TRSM_ROWS - 1) / TRSM_ROWS), TRSM_THREADS, trsm_smem(m), ctx.stream>>>(
-                W, L, m, m);
-            TRG_LAUNCHED(ctx);
-            k_small_nn<<<m, 128, 0, ctx.stream>>>(Hs, W, m, T1);
-            TRG_LAUNCHED(ctx);
-            k_small_tn<<<m, 128, 0, ctx.stream>>>(W, T1, m, G2);
-            TRG_LAUNCHED(ctx);
-            k_rr_fp64<<<1, 512, rr64_smem(m), ctx.stream>>>(G2, m, jtol, 60, theta, W, status, sweeps, full);
+            const double* Wj = W;    // the basis the FP64 sweeps start from
+            if (full) {
+                // Refine the FP32 eigenbasis in FP64 on many SMs: OA_STEPS
+                // Ogita-Aishima steps (k_oa_step), then a Lowdin step; the
+                // sweeps are left the pairs the steps could not separate.
+                double* X = W;
+                double* Xn = Xb;
+                auto small = [&](auto kern, const double* a, const double* b, double* c) {
+                    kern<<<m, 128, 0, ctx.stream>>>(a, b, m, c);
+                    TRG_LAUNCHED(ctx);
+                };
+                for (int st = 0; st < OA_STEPS; ++st) {
+                    small(k_small_nn, Hs, X, T1);      // H X
+                    small(k_small_tn, X, T1, G2);      // S = X^T H X
+                    small(k_small_tn, X, X, Pm);       // P = X^T X
+                    k_oa_step<<<1, 256, 0, ctx.stream>>>(G2, Pm, m, E);
+                    TRG_LAUNCHED(ctx);
+                    small(k_small_apply, X, E, Xn);
+                    std::swap(X, Xn);
+                }
+                small(k_small_tn, X, X, Pm);
+                small(k_small_tn, Pm, Pm, T1);          // P P (P symmetric)
+                k_lowdin<<<(m * m + 255) / 256, 256, 0, ctx.stream>>>(Pm, T1, m, E);
+                TRG_LAUNCHED(ctx);
+                small(k_small_apply, X, E, Xn);
+                std::swap(X, Xn);
+                small(k_small_nn, Hs, X, T1);
+                small(k_small_tn, X, T1, G2);          // H' = X^T H X
+                Wj = X;
+            } else {
+                // a rough Rayleigh-Ritz (no FP64 sweeps): W re-orthonormalised
+                // by Cholesky-QR, theta the diagonal of H' = W^T H W
+                k_small_tn<<<m, 128, 0, ctx.stream>>>(W, W, m, G2);
+                TRG_LAUNCHED(ctx);
+                k_chol_flag<<<1, 256, chol_smem(m), ctx.stream>>>(G2, L, m, 0.0, flags, nbad, nullptr);
+                TRG_LAUNCHED(ctx);
+                k_trsm_rows<<<(unsigned)((m + TRSM_ROWS - 1) / TRSM_ROWS), TRSM_THREADS, trsm_smem(m),
+                              ctx.stream>>>(W, L, m, m);
+                TRG_LAUNCHED(ctx);
+                k_small_nn<<<m, 128, 0, ctx.stream>>>(Hs, W, m, T1);
+                TRG_LAUNCHED(ctx);
+                k_small_tn<<<m, 128, 0, ctx.stream>>>(W, T1, m, G2);
+                TRG_LAUNCHED(ctx);
+            }
+            k_rr_fp64<<<1, 512, rr64_smem(m), ctx.stream>>>(G2, m, jtol, 60, theta, Wj, W, status, sweeps, full);
             TRG_LAUNCHED(ctx);
         }
         times_small(ctx, Y, W, n, m, Z);

@@ -216,7 +216,7 @@ namespace trg {
 void trim_buffers(Ctx& c) {
     cudaStreamSynchronize(c.stream);
     for (Buf* b : {&c.T, &c.Tnext, &c.M, &c.U, &c.ws, &c.envP, &c.envQ, &c.eig, &c.eig_small, &c.flags,
-                   &c.split_ws, &c.f64_partial, &c.cons_ef, &c.eig_slices, &c.Timp,
+                   &c.split_ws, &c.f64_partial, &c.ksplit_ws, &c.cons_ef, &c.eig_slices, &c.Timp,
                    &c.Timp_next, &c.Timp_tmp})
         c.release(*b);
     for (Buf& b : c.s3) c.release(b);

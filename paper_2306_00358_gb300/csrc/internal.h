@@ -110,6 +110,7 @@ struct Ctx {
     Buf flags;             // per-column flags (int)
     Buf split_ws;          // split GEMM: exponents and BF16 slices of both operands
     Buf f64_partial;       // FP64 GEMM: split-K partial sums
+    Buf ksplit_ws;         // split GEMM: split-K partial fixed-point sums
     Buf cons_ef;           // exponent fields recorded by a producing product (two halves)
     Buf eig_slices;        // split mode: M sliced once per isometry solve
     Buf s3[10];            // cubic-lattice step: P1, P2, Ux, Uy, Mx, My, then A, W, C, D of the contraction
@@ -174,6 +175,10 @@ struct GemmDesc {
     const int64_t* c_m;
     const int64_t* c_n;
     double beta = 0.0;      // 0: overwrite, 1: accumulate
+    // Split mode, FP64 output through staging only: the product may split K
+    // over several CTAs per tile when its tiles cannot fill the SMs (the
+    // n x m products of the isometry); exact partial sums, deterministic.
+    bool allow_ksplit = false;
     // The split epilogue may store without staging when consecutive rows are
     // adjacent in C and c_n[n + j] = c_n[n] + j c_col_stride inside each
     // aligned group of 32 columns.

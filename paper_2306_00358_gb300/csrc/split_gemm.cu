@@ -388,6 +388,13 @@ struct MmaArgs {
     // limit of the epilogue's wait for a finished accumulator chunk (the
     // other waits keep WAIT_NS); a short one lets tests reach the timeout path
     unsigned long long acc_wait_ns;
+    // split K (staged epilogue only): a unit of work is (tile, part), part p
+    // covering k blocks [p kb_per, (p + 1) kb_per) (kb_per a multiple of the
+    // 512-deep chunk); each unit stores its exact fixed-point sums V in
+    // kpart[(p N + n) M + m] and k_ksplit_reduce forms C.  ksplit = 1,
+    // kb_per >= Kp / BK: one unit per tile.
+    int ksplit, kb_per;
+    long long* kpart;
 };
 
 // Tile order: column blocks in groups of group_n; inside a group the tiles run
@@ -510,6 +517,7 @@ k_split_mma(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
     const int tiles_n = (g.N + BN - 1) / BN;
     const int num_tiles = tiles_m * tiles_n;
     const int num_kb = g.Kp / BK;
+    const int num_units = num_tiles * g.ksplit;
     // a pair shares every tile: the leader (rank 0) issues the MMAs for both,
     // and its barriers collect the loads and the drains of both CTAs
     const uint32_t rank = CG == 2 ? cluster_rank() : 0u;
@@ -557,11 +565,14 @@ k_split_mma(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
 #pragma unroll
             for (int s = 0; s < STAGES; ++s) issued[s] = -1;
             bool ok = true;
-            for (int tile = first_tile; tile < num_tiles && ok; tile += tile_step) {
+            for (int unit = first_tile; unit < num_units && ok; unit += tile_step) {
+                const int tile = unit / g.ksplit;
+                const int kb0 = (unit - tile * g.ksplit) * g.kb_per;
+                const int kb1 = min(num_kb, kb0 + g.kb_per);
                 int mb, nb;
                 tile_coords(tile, tiles_m, tiles_n, g.group_n, mb, nb);
                 const int arow = mb * TILE_M + (int)rank * BM, brow = nb * BN;
-                for (int kb = 0; kb < num_kb && ok; ++kb) {
+                for (int kb = kb0; kb < kb1 && ok; ++kb) {
                     ok = mbar_wait(&empty[stage], phase ^ 1, abort_flag, g.status);
                     if (!ok) break;
                     uint8_t* st = smem + stage * STAGE_BYTES;
@@ -610,10 +621,13 @@ k_split_mma(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
             uint32_t phase = 0;
             uint32_t chunk_no = 0;      // chunks issued so far (all tiles)
             bool ok = true;
-            for (int tile = first_tile; tile < num_tiles && ok; tile += tile_step) {
-                for (int kb = 0; kb < num_kb && ok; ++kb) {
+            for (int unit = first_tile; unit < num_units && ok; unit += tile_step) {
+                // k blocks of this unit, counted from its first (a chunk boundary)
+                const int kb0 = (unit % g.ksplit) * g.kb_per;
+                const int nkb = min(num_kb, kb0 + g.kb_per) - kb0;
+                for (int kb = 0; kb < nkb && ok; ++kb) {
                     const bool chunk_start = (kb % CHUNK_STAGES) == 0;
-                    const bool tile_end = kb + 1 == num_kb;
+                    const bool tile_end = kb + 1 == nkb;
                     const bool chunk_end = ((kb + 1) % CHUNK_STAGES) == 0 || tile_end;
                     ok = mbar_wait(&full[stage], phase, abort_flag, g.status);
                     if (!ok) break;
@@ -689,11 +703,14 @@ k_split_mma(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
         const int colh = ew >> 2;                 // which 32-column quarter
         const uint32_t lane_base = (uint32_t)(quad * 32) << 16;
         const int row_in_tile = quad * 32 + lane;
-        const int nchunks = (num_kb + CHUNK_STAGES - 1) / CHUNK_STAGES;
         uint32_t chunk_no = 0;
         uint32_t tile_iter = 0;                   // tiles done by this CTA (tags the row maxima)
         bool ok = true;
-        for (int tile = first_tile; tile < num_tiles && ok; tile += tile_step) {
+        for (int unit = first_tile; unit < num_units && ok; unit += tile_step) {
+            const int tile = unit / g.ksplit;
+            const int part = unit - tile * g.ksplit;
+            const int kb0 = part * g.kb_per;
+            const int nchunks = (min(num_kb, kb0 + g.kb_per) - kb0 + CHUNK_STAGES - 1) / CHUNK_STAGES;
             int mb, nb;
             tile_coords(tile, tiles_m, tiles_n, g.group_n, mb, nb);
             ++tile_iter;
@@ -801,6 +818,19 @@ k_split_mma(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
                         }
                         if (cur >= 0 && cur_max) atomicMax(&g.cons_ef[cur], cur_max);
                         continue;
+                    }
+                    if constexpr (MODE == EPI_STAGED) {
+                        if (g.ksplit > 1) {
+                            // split K: this part's exact sums, rows adjacent (a
+                            // warp writes 256 contiguous bytes per column)
+                            if (row_ok) {
+                                long long* dst = g.kpart + ((int64_t)part * g.N + nt) * g.M + m;
+#pragma unroll
+                                for (int j = 0; j < CPT; ++j)
+                                    if (nt + j < g.N) dst[(int64_t)j * g.M] = J[j];
+                            }
+                            continue;
+                        }
                     }
                     if constexpr (MODE == EPI_STAGED) {
                         // the FP64 results, in place
@@ -970,6 +1000,21 @@ __global__ void __launch_bounds__(256) k_row_exponent(const double* __restrict__
             atomicMax(&ef_out[r0 + threadIdx.x], rmax[threadIdx.x]);
         __syncthreads();
     }
+}
+
+// Split K: C(m, n) = the sum over the parts, in part order, of their exact
+// fixed-point sums V (kpart[(p N + n) M + m]), scaled by 2^(ea_m + eb_n - 36)
+// as the staged epilogue scales an unsplit V.
+__global__ void __launch_bounds__(256) k_ksplit_reduce(const long long* __restrict__ part, int ksplit, int M, int N,
+                                                       const int* __restrict__ ea, const int* __restrict__ eb,
+                                                       double* C, const int64_t* __restrict__ c_m,
+                                                       const int64_t* __restrict__ c_n) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= (int64_t)M * N) return;
+    const int n = (int)(i / M), m = (int)(i - (int64_t)n * M);
+    long long v = 0;
+    for (int p = 0; p < ksplit; ++p) v += part[((int64_t)p * N + n) * M + m];
+    C[c_m[m] + c_n[n]] = scaled_i64_to_double(v, ea[m] + eb[n] - 36);
 }
 
 // Convert the raw exponent fields to scale exponents e (|x| < 2^e).
@@ -1181,7 +1226,7 @@ void launch_mma_k(Ctx& ctx, const CUtensorMap& ta, const CUtensorMap& tb, const 
         }
     });
     const int tiles_m = (a.M + BM * CG - 1) / (BM * CG), tiles_n = (a.N + BN - 1) / BN;
-    const int tiles = tiles_m * tiles_n;
+    const int tiles = tiles_m * tiles_n * a.ksplit;       // units of work
     const int ctas = CG == 1 ? std::max(1, std::min(tiles, ctx.sm_count)) : 2 * std::max(1, std::min(tiles, max_clusters));
     if (a.group_n <= 0) a.group_n = choose_group_n(tiles_m * CG, tiles_n, ctas, a.Kp, S);
     cudaError_t e;
@@ -1409,6 +1454,26 @@ void gemm_split(Ctx& ctx, const GemmDesc& d) {
     a.ck_stride = d.ck_stride; a.c_rows_fast = d.c_rows_fast ? 1 : 0; a.c_col_stride = d.c_col_stride;
     // |V| <= (K / 512) (2^32 + 2^24) 2^14 + 2 K 2^20 < 2^53 for K <= 8192
     a.v_exact53 = Kp <= 8192 ? 1 : 0;
+    // split K where the tiles leave most SMs idle: a function of the shape
+    // and the SM count only (not of the CTA grouping), so every launch
+    // choice still gives the same bits
+    a.ksplit = 1; a.kb_per = Kp / BK; a.kpart = nullptr;
+    if (d.allow_ksplit && !d.cs_out && !d.c_rows_fast && !d.cons_ef) {
+        const int chunks = (Kp / BK + CHUNK_STAGES - 1) / CHUNK_STAGES;
+        const int tiles128 = ((M + BM - 1) / BM) * ((N + BN - 1) / BN);
+        if (2 * tiles128 <= ctx.sm_count && chunks >= 2) {
+            const int want = std::min(chunks, ctx.sm_count / tiles128);
+            const int per = (chunks + want - 1) / want;          // chunks per part
+            a.kb_per = per * CHUNK_STAGES;
+            a.ksplit = (chunks + per - 1) / per;
+            if (a.ksplit > 1) {
+                ctx.ensure(ctx.ksplit_ws, (size_t)a.ksplit * N * M * sizeof(long long));
+                a.kpart = ctx.ksplit_ws.as<long long>();
+            } else {
+                a.kb_per = Kp / BK;
+            }
+        }
+    }
     if (d.cs_out) {
         // a consumer row = rows_per_crow consecutive rows (32, 64 or 128, so a
         // warp's lanes and the CTA's 128-row tile hold whole groups) times
@@ -1433,10 +1498,17 @@ void gemm_split(Ctx& ctx, const GemmDesc& d) {
             case 11: launch_mma<5, 2>(ctx, ta, tb, tbh, b); break;
         }
     };
-    const TuneChoice ch = tuned_choice(ctx, M, N, Kp, S, d.cs_out ? 2 : (d.c_rows_fast ? 1 : 0), CG, launch);
+    const int mode = d.cs_out ? 2 : (d.c_rows_fast ? 1 : (a.ksplit > 1 ? 3 : 0));
+    const TuneChoice ch = tuned_choice(ctx, M, N, Kp, S, mode, CG, launch);
     const int tok = ctx.region_begin(TRG_PHASE_MMA);
     const int tok_x2 = ctx.phase == TRG_PHASE_X2 ? ctx.region_begin(TRG_PHASE_MMA_X2) : -1;
     launch(ch.cg, ch.group_n);
+    if (a.ksplit > 1) {
+        const int64_t tot = (int64_t)M * N;
+        k_ksplit_reduce<<<(unsigned)((tot + 255) / 256), 256, 0, ctx.stream>>>(a.kpart, a.ksplit, M, N, ea, eb, d.C,
+                                                                             d.c_m, d.c_n);
+        TRG_LAUNCHED(ctx);
+    }
     const double products = (double)S * (S + 1) / 2;
     ctx.region_end(tok_x2, 2.0 * (double)M * N * K, products * 2.0 * (double)M * N * Kp);
     ctx.region_end(tok, 2.0 * (double)M * N * K, products * 2.0 * (double)M * N * Kp);
@@ -1579,6 +1651,7 @@ extern "C" int trg_gemm_noalloc(int M, int N, int K, const double* A, int lda, c
         a.rows_per_crow = a.cols_per_crow = 0;
         a.ck_stride = 0; a.c_rows_fast = 0; a.c_col_stride = 0; a.v_exact53 = 0;
         a.acc_wait_ns = WAIT_NS;
+        a.ksplit = 1; a.kb_per = Kp / BK; a.kpart = nullptr;
         const int tiles = ((M + BM - 1) / BM) * ((N + BN - 1) / BN);
         const int grid = std::max(1, std::min(tiles, sms));
         a.group_n = choose_group_n((M + BM - 1) / BM, (N + BN - 1) / BN, grid, Kp, S);

@@ -14,7 +14,9 @@ dimensions 32, 48 and 64.
 * XY model (the O(2) case of Sec. 3.3, multiplet-preserving cuts) at
   beta 1.0 and 1.1, Dcut 32, 30 half-steps: the GPU against the oracle
   (tests/golden/oracle_solves_xy32.json, make_golden.py --xy32), the same
-  bounds as the Ising grid.
+  bounds as the Ising grid; the split path only where the oracle's
+  multiplet cuts are resolved at split precision (beta 1.1; at beta 1.0
+  near-degenerate levels sit within 2^-20 of the threshold).
 """
 import json
 import math
@@ -112,9 +114,33 @@ def test_xy32_fp64_matches_oracle(torch, name):
     _fp64_against(GOLDEN_XY32[name])
 
 
+def _multiplet_decisions_resolved_in_split(g, lo=1e-11, hi=5e-6):
+    """Split products separate exactly degenerate eigenvalues by up to
+    ~2^-20 lambda_1 (S = 4), so the multiplet rule treats relative gaps below
+    that as degenerate.  A solve whose oracle spectra hold a gap (at a cut
+    or between kept values) between FP64 noise and a few times that bound
+    has cuts the split path may take differently, each correctly for its
+    own spectrum; f then differs by the truncation, not by arithmetic."""
+    for st in g["steps"]:
+        if not st["truncated"]:
+            continue
+        k = st["kept"]
+        gaps = [st["gap"]] + [(k[i] - k[i + 1]) / k[0] for i in range(len(k) - 1)]
+        if any(lo < x < hi for x in gaps):
+            return False
+    return True
+
+
+def test_xy32_golden_has_a_split_resolved_case():
+    assert any(_multiplet_decisions_resolved_in_split(g) for g in GOLDEN_XY32.values())
+
+
 @pytest.mark.parametrize("name", sorted(GOLDEN_XY32))
 def test_xy32_split_matches_oracle(torch, name):
-    _split_against(GOLDEN_XY32[name])
+    g = GOLDEN_XY32[name]
+    if not _multiplet_decisions_resolved_in_split(g):
+        pytest.skip("near-degenerate levels within split precision of the multiplet threshold")
+    _split_against(g)
 
 
 @pytest.mark.slow
