@@ -343,7 +343,7 @@ int trg_destroy(trg_ctx* ctx) {
     cudaStreamSynchronize(ctx->stream);
     Ctx& c = *ctx;
     for (trg::Buf* b : {&c.T, &c.Tnext, &c.M, &c.U, &c.scal, &c.status, &c.ws, &c.envP, &c.envQ, &c.eig,
-                        &c.eig_small, &c.flags, &c.split_ws, &c.f64_partial, &c.ksplit_ws, &c.cons_ef, &c.Timp, &c.Timp_next,
+                        &c.eig_small, &c.flags, &c.split_ws, &c.f64_partial, &c.ksplit_ws, &c.bslices, &c.cons_ef, &c.Timp, &c.Timp_next,
                         &c.Timp_tmp, &c.eig_slices})
         c.release(*b);
     for (trg::Buf& b : c.s3) c.release(b);

@@ -53,6 +53,14 @@ size_t estimate_bytes(const trg_solve_spec& s, size_t workspace_cap) {
         const double rows_a = std::min(D, jb) * D * D + 128, rows_b = D2 + 128;
         bytes += (double)std::max(2, s.split_slices) * (rows_a + rows_b) * (D2 + 32) * 2 + (rows_a + rows_b) * 4;
         bytes += (double)std::max(2, s.split_slices) * (D2 + 256) * (D2 + 32) * 2;   // M sliced for the isometry
+        // the contraction's operands shared by its j-blocks (t as B, U twice)
+        const double S_ = std::max(2, s.split_slices);
+        bytes += S_ * (D2 + 128) * (D2 + 32) * 2 +          // t as the D^7 product's B
+                 S_ * (D2 + 256) * (D + 32) * 2 +           // U as X1's A (D Dn rows, K = D)
+                 S_ * (D + 128) * (D2 + 32) * 2 +           // U as the last product's B
+                 3 * (D2 + 256) * 4 + 3 * 256.0;            // their exponents, alignment
+        // split-K parts of the isometry's products: at most 152 x 128 rows x m
+        bytes += 152.0 * 128 * m * 8;
     }
     bytes += 64.0 * 1024 * 1024;               // tables, scalars, allocator slack
     return (size_t)bytes;
@@ -216,7 +224,7 @@ namespace trg {
 void trim_buffers(Ctx& c) {
     cudaStreamSynchronize(c.stream);
     for (Buf* b : {&c.T, &c.Tnext, &c.M, &c.U, &c.ws, &c.envP, &c.envQ, &c.eig, &c.eig_small, &c.flags,
-                   &c.split_ws, &c.f64_partial, &c.ksplit_ws, &c.cons_ef, &c.eig_slices, &c.Timp,
+                   &c.split_ws, &c.f64_partial, &c.ksplit_ws, &c.bslices, &c.cons_ef, &c.eig_slices, &c.Timp,
                    &c.Timp_next, &c.Timp_tmp})
         c.release(*b);
     for (Buf& b : c.s3) c.release(b);

@@ -111,6 +111,7 @@ struct Ctx {
     Buf split_ws;          // split GEMM: exponents and BF16 slices of both operands
     Buf f64_partial;       // FP64 GEMM: split-K partial sums
     Buf ksplit_ws;         // split GEMM: split-K partial fixed-point sums
+    Buf bslices;           // contraction: the D^7 product's B slices, shared by its j-blocks
     Buf cons_ef;           // exponent fields recorded by a producing product (two halves)
     Buf eig_slices;        // split mode: M sliced once per isometry solve
     Buf s3[10];            // cubic-lattice step: P1, P2, Ux, Uy, Mx, My, then A, W, C, D of the contraction
@@ -209,6 +210,10 @@ struct GemmDesc {
     int64_t ck_stride = 0;  // consumer column of producer column n + 1 minus that of n, inside a row group
     const uint16_t* a_slices = nullptr;
     const int* a_e = nullptr;
+    // Split mode: B arrives sliced (split_slice_b), for a B that several
+    // products share; the product then skips B's exponent and slicing passes.
+    const uint16_t* b_slices = nullptr;
+    const int* b_e = nullptr;
 };
 // Rows and columns of the padded slice arrays a split product of M rows and
 // K columns reads for its A operand (the fused hand-over writes this layout).
@@ -216,6 +221,10 @@ int64_t split_rows_padded(const Ctx& ctx, int64_t M);
 int64_t split_k_padded(int64_t K);
 // Slice an A operand once for several split products (GemmDesc::a_slices / a_e).
 void split_slice_operand(Ctx& ctx, const Gather& A, int64_t M, int64_t K, uint16_t* slices, int* e);
+// Exponents (per column n) and BF16 slices of a K x N B operand in the layout
+// a split product reads: [S][split_cols_padded(N)][split_k_padded(K)].
+void split_slice_b(Ctx& ctx, const Gather& B, int64_t K, int64_t N, uint16_t* slices, int* e);
+int64_t split_cols_padded(int64_t N);
 void gemm(Ctx& ctx, const GemmDesc& g, int precision);
 void gemm_f64(Ctx& ctx, const GemmDesc& g);
 

@@ -185,6 +185,44 @@ void contract(Ctx& ctx, const View4& top, const View4& bottom, const double* U, 
         ef3 = ef2 + rows2;
     }
 
+    // Operands that are the same for every j-block -- U as X1's A, the
+    // bottom tensor as the D^7 product's B, U as the last product's B -- are
+    // sliced once, before the first block, when there are several blocks.
+    const Gather a1 = gather(ctx, U, {{Dn, 1}, {Dx, Dx * Dn}}, {{Dx, Dn}});
+    const Gather b2 = gather(ctx, bottom.p, {{Dy, sb[1]}, {Dx, sb[0]}}, {{Dy, sb[3]}, {Dx, sb[2]}});
+    const Gather b3 = gather(ctx, U, {{Dx, Dx * Dn}, {Dx, Dn}}, {{Dn, 1}});
+    struct Pre { const uint16_t* s = nullptr; const int* e = nullptr; } p1, p2, p3;
+    if (split && j_end - j_begin > jb) {
+        auto bytes = [](int64_t rows, int64_t k, int S_) {
+            const size_t sl = ((size_t)S_ * rows * split_k_padded(k) * 2 + 255) & ~(size_t)255;
+            return sl + (((size_t)rows * sizeof(int) + 255) & ~(size_t)255);
+        };
+        const int64_t r1 = split_rows_padded(ctx, Dx * Dn), r2 = split_cols_padded(DD), r3 = split_cols_padded(Dn);
+        const size_t n1 = bytes(r1, Dx, S), n2 = bytes(r2, DD, S), n3 = bytes(r3, Dx * Dx, S);
+        ctx.ensure(ctx.bslices, n1 + n2 + n3);
+        uint8_t* base = ctx.bslices.as<uint8_t>();
+        auto place = [&](uint8_t* at, int64_t rows, int64_t k, Pre& p) {
+            const size_t sl = ((size_t)S * rows * split_k_padded(k) * 2 + 255) & ~(size_t)255;
+            p.s = (const uint16_t*)at;
+            p.e = (const int*)(at + sl);
+        };
+        place(base, r1, Dx, p1);
+        place(base + n1, r2, DD, p2);
+        place(base + n1 + n2, r3, Dx * Dx, p3);
+        ctx.phase = TRG_PHASE_X1;
+        int tok = ctx.region_begin(TRG_PHASE_X1);
+        split_slice_operand(ctx, a1, Dx * Dn, Dx, const_cast<uint16_t*>(p1.s), const_cast<int*>(p1.e));
+        ctx.region_end(tok, 0.0, 0.0);
+        ctx.phase = TRG_PHASE_X2;
+        tok = ctx.region_begin(TRG_PHASE_X2);
+        split_slice_b(ctx, b2, DD, DD, const_cast<uint16_t*>(p2.s), const_cast<int*>(p2.e));
+        ctx.region_end(tok, 0.0, 0.0);
+        ctx.phase = TRG_PHASE_X3;
+        tok = ctx.region_begin(TRG_PHASE_X3);
+        split_slice_b(ctx, b3, Dx * Dx, Dn, const_cast<uint16_t*>(p3.s), const_cast<int*>(p3.e));
+        ctx.region_end(tok, 0.0, 0.0);
+    }
+
     for (int64_t j0 = j_begin; j0 < j_end; j0 += jb) {
         const int64_t jn = std::min(jb, j_end - j0);
         const int64_t M2 = jn * Dn * Dx, M3 = jn * Dn * Dy;       // rows of this block's X2 / O products
@@ -193,7 +231,9 @@ void contract(Ctx& ctx, const View4& top, const View4& bottom, const double* U, 
             ctx.phase = TRG_PHASE_X1;
             GemmDesc g;
             g.M = Dx * Dn; g.N = jn * DD; g.K = Dx;
-            g.A = gather(ctx, U, {{Dn, 1}, {Dx, Dx * Dn}}, {{Dx, Dn}});
+            g.A = a1;
+            g.a_slices = p1.s;
+            g.a_e = p1.e;
             g.B = gather(ctx, t.p + j0 * s[1], {{Dx, s[0]}}, {{jb, s[1]}, {Dx, s[2]}, {Dy, s[3]}});
             // consumer row of element ((i,a),(jj,d,c)) is (jj,i,d), its column c Dx + a
             g.cons_m = ctx.table({{Dn, Dx}, {Dx, 0}});
@@ -230,7 +270,9 @@ void contract(Ctx& ctx, const View4& top, const View4& bottom, const double* U, 
             GemmDesc g;
             g.M = M2; g.N = DD; g.K = DD;
             g.A = gather(ctx, X1, {{jb * Dn * Dx, DD}}, {{DD, 1}});
-            g.B = gather(ctx, bottom.p, {{Dy, sb[1]}, {Dx, sb[0]}}, {{Dy, sb[3]}, {Dx, sb[2]}});
+            g.B = b2;
+            g.b_slices = p2.s;
+            g.b_e = p2.e;
             // consumer row of element ((jj,i,d),(l,e)) is (jj,i,l), its column e Dx + d
             g.cons_m = ctx.table({{jb * Dn, Dy}, {Dx, 0}});
             g.cons_n = ctx.table({{Dy, 1}, {Dx, 0}});
@@ -271,7 +313,9 @@ void contract(Ctx& ctx, const View4& top, const View4& bottom, const double* U, 
             GemmDesc g;
             g.M = M3; g.N = Dn; g.K = Dx * Dx;
             g.A = gather(ctx, X2, {{jb * Dn * Dy, Dx * Dx}}, {{Dx * Dx, 1}});
-            g.B = gather(ctx, U, {{Dx, Dx * Dn}, {Dx, Dn}}, {{Dn, 1}});
+            g.B = b3;
+            g.b_slices = p3.s;
+            g.b_e = p3.e;
             g.C = out.p + (j0 - j_out0) * o[1];
             g.c_m = ctx.table({{jb, o[1]}, {Dn, o[0]}, {Dy, o[3]}});
             g.c_n = ctx.table({{Dn, o[2]}});

@@ -109,7 +109,7 @@ __host__ __device__ constexpr int smem_bytes_for(int S, int CG, int MODE) {
 constexpr bool smem_fits() {
     for (int S = 2; S <= 5; ++S)
         for (int CG = 1; CG <= 2; ++CG)
-            for (int MODE = 0; MODE <= 2; ++MODE)
+            for (int MODE = 0; MODE <= 3; ++MODE)
                 if (smem_bytes_for(S, CG, MODE) > SMEM_LIMIT || stages_for(S, CG, MODE) < 2) return false;
     return true;
 }
@@ -299,6 +299,19 @@ __device__ __forceinline__ double scaled_i64_to_double(long long v, int e2) {
     return __longlong_as_double((long long)bits);
 }
 
+// The same for |v| < 2^53 (the value is exact: no rounding step).
+__device__ __forceinline__ double scaled_i64_to_double_exact(long long v, int e2) {
+    if (v == 0) return 0.0;
+    const unsigned long long sign = v < 0 ? (1ull << 63) : 0ull;
+    const unsigned long long a = v < 0 ? (unsigned long long)(-v) : (unsigned long long)v;
+    const int top = 63 - __clzll((long long)a);
+    const int ex = top + e2;
+    if (ex < -1022) return __longlong_as_double((long long)sign);
+    if (ex > 1023) return __longlong_as_double((long long)(sign | 0x7FF0000000000000ull));
+    const unsigned long long mant = a << (52 - top);
+    return __longlong_as_double((long long)(sign | ((unsigned long long)(ex + 1023) << 52) | (mant & ((1ull << 52) - 1))));
+}
+
 // |v| rounded to 53 significant bits (half to even), as the FP64 value of v
 // has it, and the position of its leading one afterwards.
 __device__ __forceinline__ unsigned long long round53(unsigned long long a, int& top) {
@@ -388,7 +401,7 @@ struct MmaArgs {
     // limit of the epilogue's wait for a finished accumulator chunk (the
     // other waits keep WAIT_NS); a short one lets tests reach the timeout path
     unsigned long long acc_wait_ns;
-    // split K (staged epilogue only): a unit of work is (tile, part), part p
+    // split K (EPI_KSPLIT): a unit of work is (tile, part), part p
     // covering k blocks [p kb_per, (p + 1) kb_per) (kb_per a multiple of the
     // 512-deep chunk); each unit stores its exact fixed-point sums V in
     // kpart[(p N + n) M + m] and k_ksplit_reduce forms C.  ksplit = 1,
@@ -487,7 +500,7 @@ static_assert(pair_table_ok(2) && pair_table_ok(3) && pair_table_ok(4) && pair_t
 // adjacent in C), stored directly (rows adjacent in C), or the consumer's
 // slices (fused hand-over).  One kernel instance each keeps the register
 // allocation of each epilogue to itself.
-enum EpiMode { EPI_STAGED = 0, EPI_DIRECT = 1, EPI_FUSED = 2 };
+enum EpiMode { EPI_STAGED = 0, EPI_DIRECT = 1, EPI_FUSED = 2, EPI_KSPLIT = 3 };
 
 template <int S, int CG, int MODE>
 __global__ void __launch_bounds__(THREADS, 1)
@@ -800,7 +813,8 @@ k_split_mma(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
                             const int e2 = ea + __shfl_sync(0xffffffffu, eb_l, j);
                             const long long cn = __shfl_sync(0xffffffffu, cn_l, j);
                             if (row_ok && nt + j < g.N) {
-                                const double v = scaled_i64_to_double(J[j], e2);
+                                const double v = g.v_exact53 ? scaled_i64_to_double_exact(J[j], e2)
+                                                             : scaled_i64_to_double(J[j], e2);
                                 *cp = v;
                                 if (g.cons_ef) {
                                     const int64_t crow = cm0 + cn;
@@ -819,18 +833,17 @@ k_split_mma(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
                         if (cur >= 0 && cur_max) atomicMax(&g.cons_ef[cur], cur_max);
                         continue;
                     }
-                    if constexpr (MODE == EPI_STAGED) {
-                        if (g.ksplit > 1) {
-                            // split K: this part's exact sums, rows adjacent (a
-                            // warp writes 256 contiguous bytes per column)
-                            if (row_ok) {
-                                long long* dst = g.kpart + ((int64_t)part * g.N + nt) * g.M + m;
+                    if constexpr (MODE == EPI_KSPLIT) {
+                        // split K: this part's exact sums, rows adjacent (a warp
+                        // writes 256 contiguous bytes per column); k_ksplit_reduce
+                        // forms the FP64 results
+                        if (row_ok) {
+                            long long* dst = g.kpart + ((int64_t)part * g.N + nt) * g.M + m;
 #pragma unroll
-                                for (int j = 0; j < CPT; ++j)
-                                    if (nt + j < g.N) dst[(int64_t)j * g.M] = J[j];
-                            }
-                            continue;
+                            for (int j = 0; j < CPT; ++j)
+                                if (nt + j < g.N) dst[(int64_t)j * g.M] = J[j];
                         }
+                        continue;
                     }
                     if constexpr (MODE == EPI_STAGED) {
                         // the FP64 results, in place
@@ -1266,6 +1279,7 @@ template <int S, int CG>
 void launch_mma(Ctx& ctx, const CUtensorMap& ta, const CUtensorMap& tb, const CUtensorMap& tbh, const MmaArgs& a) {
     if (a.cs_out) launch_mma_k<S, CG, EPI_FUSED>(ctx, ta, tb, tbh, a);
     else if (a.c_rows_fast) launch_mma_k<S, CG, EPI_DIRECT>(ctx, ta, tb, tbh, a);
+    else if (a.ksplit > 1) launch_mma_k<S, CG, EPI_KSPLIT>(ctx, ta, tb, tbh, a);
     else launch_mma_k<S, CG, EPI_STAGED>(ctx, ta, tb, tbh, a);
 }
 
@@ -1318,6 +1332,24 @@ void split_slice_operand(Ctx& ctx, const Gather& A, int64_t M, int64_t K, uint16
         default: fail(TRG_EINVAL, "split_slices must be 2..5");
     }
 }
+
+// Exponents and BF16 slices of a B operand (K x N) as a split product reads
+// it: rows n of B^T, padded to the 128-column tile.
+void split_slice_b(Ctx& ctx, const Gather& B, int64_t K, int64_t N, uint16_t* slices, int* e) {
+    const int S = slices_now(ctx);
+    const int Ni = (int)N, Ki = (int)std::max<int64_t>(K, 1);
+    const int Np = (int)split_cols_padded(N), Kp = (int)split_k_padded(K);
+    const Gather bt = transpose_gather(B, B.off_r, B.off_c);
+    row_exponents(ctx, bt, Ni, Ki, e);
+    switch (S) {
+        case 2: launch_slice<2>(ctx, bt, Ni, Ki, Np, Kp, e, slices); break;
+        case 3: launch_slice<3>(ctx, bt, Ni, Ki, Np, Kp, e, slices); break;
+        case 4: launch_slice<4>(ctx, bt, Ni, Ki, Np, Kp, e, slices); break;
+        case 5: launch_slice<5>(ctx, bt, Ni, Ki, Np, Kp, e, slices); break;
+        default: fail(TRG_EINVAL, "split_slices must be 2..5");
+    }
+}
+int64_t split_cols_padded(int64_t N) { return (N + BN - 1) / BN * BN; }
 
 int64_t split_rows_padded(const Ctx& ctx, int64_t M) {
     const int64_t tile = (ctx.cfg.mma_pairs && M > BM) ? 2 * BM : BM;
@@ -1401,16 +1433,18 @@ void gemm_split(Ctx& ctx, const GemmDesc& d) {
     const int CG = (ctx.cfg.mma_pairs && M > BM) ? 2 : 1;
     const int Mp = (int)split_rows_padded(ctx, M), Np = (N + BN - 1) / BN * BN, Kp = (int)split_k_padded(K);
     const bool pre_a = d.a_slices != nullptr;    // A arrives sliced from its producer
+    const bool pre_b = d.b_slices != nullptr;    // B arrives sliced (shared by several products)
 
-    // scratch: exponents + slices of A (unless given) and B
+    // scratch: exponents + slices of A and B (unless given)
     const size_t bytes_e = (size_t)(Mp + Np) * sizeof(int);
-    const size_t bytes_a = pre_a ? 0 : (size_t)S * Mp * Kp * 2, bytes_b = (size_t)S * Np * Kp * 2;
+    const size_t bytes_a = pre_a ? 0 : (size_t)S * Mp * Kp * 2, bytes_b = pre_b ? 0 : (size_t)S * Np * Kp * 2;
     ctx.ensure(ctx.split_ws, bytes_e + bytes_a + bytes_b + 1024);
     uint8_t* base = ctx.split_ws.as<uint8_t>();
     int* ea = pre_a ? const_cast<int*>(d.a_e) : (int*)base;
-    int* eb = (int*)base + Mp;
+    int* eb = pre_b ? const_cast<int*>(d.b_e) : (int*)base + Mp;
     uint16_t* sa = pre_a ? const_cast<uint16_t*>(d.a_slices) : (uint16_t*)(base + ((bytes_e + 255) & ~(size_t)255));
-    uint16_t* sb = (uint16_t*)(base + ((bytes_e + 255) & ~(size_t)255)) + (pre_a ? 0 : (size_t)S * Mp * Kp);
+    uint16_t* sb = pre_b ? const_cast<uint16_t*>(d.b_slices)
+                         : (uint16_t*)(base + ((bytes_e + 255) & ~(size_t)255)) + (pre_a ? 0 : (size_t)S * Mp * Kp);
 
     // B as rows n, columns k: element (n, k) at B[b_k[k] + b_n[n]]
     const Gather bt = transpose_gather(d.B, d.B.off_r, d.B.off_c);
@@ -1427,16 +1461,16 @@ void gemm_split(Ctx& ctx, const GemmDesc& d) {
     } else {
         row_exponents(ctx, d.A, M, K, ea);
     }
-    row_exponents(ctx, bt2, N, K, eb);
+    if (!pre_b) row_exponents(ctx, bt2, N, K, eb);
     switch (S) {
         case 2: if (!pre_a) launch_slice<2>(ctx, d.A, M, K, Mp, Kp, ea, sa);
-                launch_slice<2>(ctx, bt2, N, K, Np, Kp, eb, sb); break;
+                if (!pre_b) launch_slice<2>(ctx, bt2, N, K, Np, Kp, eb, sb); break;
         case 3: if (!pre_a) launch_slice<3>(ctx, d.A, M, K, Mp, Kp, ea, sa);
-                launch_slice<3>(ctx, bt2, N, K, Np, Kp, eb, sb); break;
+                if (!pre_b) launch_slice<3>(ctx, bt2, N, K, Np, Kp, eb, sb); break;
         case 4: if (!pre_a) launch_slice<4>(ctx, d.A, M, K, Mp, Kp, ea, sa);
-                launch_slice<4>(ctx, bt2, N, K, Np, Kp, eb, sb); break;
+                if (!pre_b) launch_slice<4>(ctx, bt2, N, K, Np, Kp, eb, sb); break;
         case 5: if (!pre_a) launch_slice<5>(ctx, d.A, M, K, Mp, Kp, ea, sa);
-                launch_slice<5>(ctx, bt2, N, K, Np, Kp, eb, sb); break;
+                if (!pre_b) launch_slice<5>(ctx, bt2, N, K, Np, Kp, eb, sb); break;
         default: fail(TRG_EINVAL, "split_slices must be 2..5");
     }
     const CUtensorMap ta = make_map(sa, S * Mp, Kp);
