@@ -115,7 +115,8 @@ struct Ctx {
     Buf cons_ef;           // exponent fields recorded by a producing product (two halves)
     Buf eig_slices;        // split mode: M sliced once per isometry solve
     Buf s3[10];            // cubic-lattice step: P1, P2, Ux, Uy, Mx, My, then A, W, C, D of the contraction
-    std::map<std::string, Buf> tables;  // cached offset tables
+    std::map<std::string, Buf> tables;  // cached offset tables (and tile lists)
+    std::map<std::string, int> list_len;   // entries of the cached tile lists
 
     // ---- phase timing
     bool prof = false;
@@ -210,6 +211,13 @@ struct GemmDesc {
     int64_t ck_stride = 0;  // consumer column of producer column n + 1 minus that of n, inside a row group
     const uint16_t* a_slices = nullptr;
     const int* a_e = nullptr;
+    // C = A A^T (a Gram product): B is A read the other way (B(k, n) =
+    // A(n, k)), M = N, and c_m, c_n address C for either index.  Split mode
+    // slices A once for both operands (when their padded sizes agree),
+    // computes only the tiles that reach the diagonal or above it, and
+    // writes each element above the diagonal also at its mirror position,
+    // so C is exactly symmetric; FP64 mode computes all of C.
+    bool gram = false;
     // Split mode: B arrives sliced (split_slice_b), for a B that several
     // products share; the product then skips B's exponent and slicing passes.
     const uint16_t* b_slices = nullptr;

@@ -102,6 +102,7 @@ void environment(Ctx& ctx, const View4& t, double* M, int precision) {
         g.B = gather(ctx, t.p, k, r);
         g.C = P; g.c_m = ctx.table({{DD, DD}}); g.c_n = ctx.table({{DD, 1}});
         g.beta = 0.0;
+        g.gram = true;          // P = A A^T (the SYRK of the environment)
         gemm(ctx, g, precision);
     }
     {   // Q: rows (i,e), k (c,d), cols (k,f)
@@ -112,6 +113,7 @@ void environment(Ctx& ctx, const View4& t, double* M, int precision) {
         g.B = gather(ctx, t.p, k, r);
         g.C = Q; g.c_m = ctx.table({{DD, DD}}); g.c_n = ctx.table({{DD, 1}});
         g.beta = 0.0;
+        g.gram = true;          // Q = A A^T
         gemm(ctx, g, precision);
     }
     {   // M: rows (i,k), k (e,f), cols (j,l); stored M[(i,j),(k,l)]

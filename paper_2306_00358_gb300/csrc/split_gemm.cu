@@ -408,6 +408,13 @@ struct MmaArgs {
     // kb_per >= Kp / BK: one unit per tile.
     int ksplit, kb_per;
     long long* kpart;
+    // optional list of the tiles to compute (mb << 32 | nb), in order; with
+    // sym, C is symmetric and the list holds the tiles that reach the
+    // diagonal or above: elements above the diagonal are written at (m, n)
+    // and at (n, m), those below it not at all (their mirrors are)
+    const long long* tile_list;
+    int n_list;
+    int sym;
 };
 
 // Tile order: column blocks in groups of group_n; inside a group the tiles run
@@ -415,6 +422,18 @@ struct MmaArgs {
 // grid / group_n row blocks of A and group_n column blocks of B, a working
 // set the host sizes to stay in L2 (a plain row-major order over many column
 // blocks streams all of B through L2 once per wave).
+__device__ __forceinline__ void tile_coords(int tile, int tiles_m, int tiles_n, int group_n, int& mb, int& nb);
+// Row and column block of the tile-th tile of a launch (a listed tile, or
+// the tile order of tile_coords).
+__device__ __forceinline__ void unit_tile(const MmaArgs& g, int tile, int tiles_m, int tiles_n, int& mb, int& nb) {
+    if (g.tile_list) {
+        const long long v = g.tile_list[tile];
+        mb = (int)(v >> 32);
+        nb = (int)(v & 0xffffffffll);
+    } else {
+        tile_coords(tile, tiles_m, tiles_n, g.group_n, mb, nb);
+    }
+}
 __device__ __forceinline__ void tile_coords(int tile, int tiles_m, int tiles_n, int group_n, int& mb, int& nb) {
     const int per_group = tiles_m * group_n;
     const int group = tile / per_group;
@@ -528,7 +547,7 @@ k_split_mma(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
     const int lane = threadIdx.x & 31;
     const int tiles_m = (g.M + TILE_M - 1) / TILE_M;
     const int tiles_n = (g.N + BN - 1) / BN;
-    const int num_tiles = tiles_m * tiles_n;
+    const int num_tiles = g.tile_list ? g.n_list : tiles_m * tiles_n;
     const int num_kb = g.Kp / BK;
     const int num_units = num_tiles * g.ksplit;
     // a pair shares every tile: the leader (rank 0) issues the MMAs for both,
@@ -583,7 +602,7 @@ k_split_mma(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
                 const int kb0 = (unit - tile * g.ksplit) * g.kb_per;
                 const int kb1 = min(num_kb, kb0 + g.kb_per);
                 int mb, nb;
-                tile_coords(tile, tiles_m, tiles_n, g.group_n, mb, nb);
+                unit_tile(g, tile, tiles_m, tiles_n, mb, nb);
                 const int arow = mb * TILE_M + (int)rank * BM, brow = nb * BN;
                 for (int kb = kb0; kb < kb1 && ok; ++kb) {
                     ok = mbar_wait(&empty[stage], phase ^ 1, abort_flag, g.status);
@@ -725,7 +744,7 @@ k_split_mma(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
             const int kb0 = part * g.kb_per;
             const int nchunks = (min(num_kb, kb0 + g.kb_per) - kb0 + CHUNK_STAGES - 1) / CHUNK_STAGES;
             int mb, nb;
-            tile_coords(tile, tiles_m, tiles_n, g.group_n, mb, nb);
+            unit_tile(g, tile, tiles_m, tiles_n, mb, nb);
             ++tile_iter;
             const int row0 = mb * TILE_M + (int)rank * BM;   // this CTA's rows of the tile
             // J = I0 2^8 + I1: the exact ACC0 and ACC1 sums of this tile's
@@ -942,6 +961,17 @@ k_split_mma(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
                         if (cur >= 0 && cur_max) atomicMax(&g.cons_ef[cur], cur_max);
                     }
                     if (MODE == EPI_FUSED) continue;
+                    if (MODE == EPI_STAGED && g.sym && row_ok) {
+                        // symmetric C: the mirror (n, m) of each element above the
+                        // diagonal (adjacent lanes, adjacent rows m: contiguous in
+                        // a row of C)
+                        const int64_t cm_mirror = g.c_n[m];
+#pragma unroll
+                        for (int j = 0; j < CPT; ++j) {
+                            const int n = nt + j;
+                            if (n < g.N && n > m) g.C[g.c_m[n] + cm_mirror] = __longlong_as_double(J[j]);
+                        }
+                    }
                     // stores through the warp's 32 x 8 staging tile: lanes of a
                     // quarter-warp then write 8 adjacent columns (64 B) of one row
                     double* stg = staging + ew * (32 * 8);
@@ -958,7 +988,8 @@ k_split_mma(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
                         for (int q = 0; q < 8; ++q) {
                             const int rr = 4 * q + quarter;
                             const int mr = row0 + quad * 32 + rr;
-                            if (mr < g.M && n < g.N) g.C[g.c_m[mr] + cn] = stg[rr * 8 + (cl ^ ((rr >> 1) & 7))];
+                            if (mr < g.M && n < g.N && (!g.sym || n >= mr))
+                                g.C[g.c_m[mr] + cn] = stg[rr * 8 + (cl ^ ((rr >> 1) & 7))];
                         }
                         __syncwarp();
                     }
@@ -1196,6 +1227,17 @@ CUtensorMap make_map(const void* base, int rows, int kp, int box_rows = BM) {
 // then streams on; the column blocks of B are re-read by every wave of the
 // group and stay in L2 only if group_n of them fit.  Pick the group width
 // with the fewest operand bytes read from DRAM under that model.
+// tile_coords on the host (the symmetric products' tile lists)
+static void tile_coords_host(int tile, int tiles_m, int tiles_n, int group_n, int& mb, int& nb) {
+    const int per_group = tiles_m * group_n;
+    const int group = tile / per_group;
+    const int first_n = group * group_n;
+    const int width = std::min(group_n, tiles_n - first_n);
+    const int local = tile - group * per_group;
+    mb = local / width;
+    nb = first_n + local % width;
+}
+
 int choose_group_n(int tiles_m, int tiles_n, int grid, int kp, int S) {
     const double block = (double)BM * kp * S * 2;            // bytes of one 128-row slice block
     const double budget = 80.0 * (1 << 20);
@@ -1239,7 +1281,7 @@ void launch_mma_k(Ctx& ctx, const CUtensorMap& ta, const CUtensorMap& tb, const 
         }
     });
     const int tiles_m = (a.M + BM * CG - 1) / (BM * CG), tiles_n = (a.N + BN - 1) / BN;
-    const int tiles = tiles_m * tiles_n * a.ksplit;       // units of work
+    const int tiles = (a.tile_list ? a.n_list : tiles_m * tiles_n) * a.ksplit;   // units of work
     const int ctas = CG == 1 ? std::max(1, std::min(tiles, ctx.sm_count)) : 2 * std::max(1, std::min(tiles, max_clusters));
     if (a.group_n <= 0) a.group_n = choose_group_n(tiles_m * CG, tiles_n, ctas, a.Kp, S);
     cudaError_t e;
@@ -1433,7 +1475,11 @@ void gemm_split(Ctx& ctx, const GemmDesc& d) {
     const int CG = (ctx.cfg.mma_pairs && M > BM) ? 2 : 1;
     const int Mp = (int)split_rows_padded(ctx, M), Np = (N + BN - 1) / BN * BN, Kp = (int)split_k_padded(K);
     const bool pre_a = d.a_slices != nullptr;    // A arrives sliced from its producer
-    const bool pre_b = d.b_slices != nullptr;    // B arrives sliced (shared by several products)
+    if (d.gram && (M != N || d.b_slices || pre_a || d.cs_out || d.cons_ef || d.c_rows_fast))
+        fail(TRG_EINVAL, "split GEMM: a Gram product takes a square C and plain operands");
+    // a Gram product reads A's slices for B too (same rows, same padding)
+    const bool gram_b = d.gram && Mp == Np;
+    const bool pre_b = d.b_slices != nullptr || gram_b;   // B arrives sliced (shared by several products)
 
     // scratch: exponents + slices of A and B (unless given)
     const size_t bytes_e = (size_t)(Mp + Np) * sizeof(int);
@@ -1441,9 +1487,10 @@ void gemm_split(Ctx& ctx, const GemmDesc& d) {
     ctx.ensure(ctx.split_ws, bytes_e + bytes_a + bytes_b + 1024);
     uint8_t* base = ctx.split_ws.as<uint8_t>();
     int* ea = pre_a ? const_cast<int*>(d.a_e) : (int*)base;
-    int* eb = pre_b ? const_cast<int*>(d.b_e) : (int*)base + Mp;
+    int* eb = gram_b ? ea : pre_b ? const_cast<int*>(d.b_e) : (int*)base + Mp;
     uint16_t* sa = pre_a ? const_cast<uint16_t*>(d.a_slices) : (uint16_t*)(base + ((bytes_e + 255) & ~(size_t)255));
-    uint16_t* sb = pre_b ? const_cast<uint16_t*>(d.b_slices)
+    uint16_t* sb = gram_b ? sa
+                 : pre_b ? const_cast<uint16_t*>(d.b_slices)
                          : (uint16_t*)(base + ((bytes_e + 255) & ~(size_t)255)) + (pre_a ? 0 : (size_t)S * Mp * Kp);
 
     // B as rows n, columns k: element (n, k) at B[b_k[k] + b_n[n]]
@@ -1492,7 +1539,8 @@ void gemm_split(Ctx& ctx, const GemmDesc& d) {
     // and the SM count only (not of the CTA grouping), so every launch
     // choice still gives the same bits
     a.ksplit = 1; a.kb_per = Kp / BK; a.kpart = nullptr;
-    if (d.allow_ksplit && !d.cs_out && !d.c_rows_fast && !d.cons_ef) {
+    a.tile_list = nullptr; a.n_list = 0; a.sym = d.gram ? 1 : 0;
+    if (d.allow_ksplit && !d.cs_out && !d.c_rows_fast && !d.cons_ef && !d.gram) {
         const int chunks = (Kp / BK + CHUNK_STAGES - 1) / CHUNK_STAGES;
         const int tiles128 = ((M + BM - 1) / BM) * ((N + BN - 1) / BN);
         if (2 * tiles128 <= ctx.sm_count && chunks >= 2) {
@@ -1521,6 +1569,32 @@ void gemm_split(Ctx& ctx, const GemmDesc& d) {
     auto launch = [&](int cg, int group_n) {
         MmaArgs b = a;
         b.group_n = group_n;
+        if (d.gram) {
+            // the tiles that reach the diagonal or above, in tile_coords order
+            const int tile_m = BM * cg, tiles_m = (M + tile_m - 1) / tile_m, tiles_n = (N + BN - 1) / BN;
+            const int gn = group_n > 0 ? group_n : tiles_n;
+            b.group_n = gn;
+            const std::string key = "sym:" + std::to_string(tiles_m) + ":" + std::to_string(tiles_n) + ":" +
+                                    std::to_string(gn) + ":" + std::to_string(tile_m);
+            auto it = ctx.tables.find(key);
+            if (it == ctx.tables.end()) {
+                std::vector<long long> h;
+                for (int t = 0; t < tiles_m * tiles_n; ++t) {
+                    int mb, nb;
+                    tile_coords_host(t, tiles_m, tiles_n, gn, mb, nb);
+                    if ((int64_t)nb * BN + BN - 1 >= (int64_t)mb * tile_m) h.push_back(((long long)mb << 32) | nb);
+                }
+                Buf buf;
+                ctx.ensure(buf, h.size() * sizeof(long long));
+                TRG_CUDA(cudaMemcpyAsync(buf.p, h.data(), h.size() * sizeof(long long), cudaMemcpyHostToDevice,
+                                         ctx.stream));
+                TRG_CUDA(cudaStreamSynchronize(ctx.stream));   // h dies here
+                it = ctx.tables.emplace(key, buf).first;
+                ctx.list_len[key] = (int)h.size();
+            }
+            b.tile_list = it->second.as<long long>();
+            b.n_list = ctx.list_len[key];
+        }
         switch (S * 2 + cg - 1) {
             case 4: launch_mma<2, 1>(ctx, ta, tb, tbh, b); break;
             case 5: launch_mma<2, 2>(ctx, ta, tb, tbh, b); break;
@@ -1532,7 +1606,7 @@ void gemm_split(Ctx& ctx, const GemmDesc& d) {
             case 11: launch_mma<5, 2>(ctx, ta, tb, tbh, b); break;
         }
     };
-    const int mode = d.cs_out ? 2 : (d.c_rows_fast ? 1 : (a.ksplit > 1 ? 3 : 0));
+    const int mode = d.cs_out ? 2 : (d.c_rows_fast ? 1 : (a.ksplit > 1 ? 3 : (d.gram ? 4 : 0)));
     const TuneChoice ch = tuned_choice(ctx, M, N, Kp, S, mode, CG, launch);
     const int tok = ctx.region_begin(TRG_PHASE_MMA);
     const int tok_x2 = ctx.phase == TRG_PHASE_X2 ? ctx.region_begin(TRG_PHASE_MMA_X2) : -1;
@@ -1686,6 +1760,7 @@ extern "C" int trg_gemm_noalloc(int M, int N, int K, const double* A, int lda, c
         a.ck_stride = 0; a.c_rows_fast = 0; a.c_col_stride = 0; a.v_exact53 = 0;
         a.acc_wait_ns = WAIT_NS;
         a.ksplit = 1; a.kb_per = Kp / BK; a.kpart = nullptr;
+        a.tile_list = nullptr; a.n_list = 0; a.sym = 0;
         const int tiles = ((M + BM - 1) / BM) * ((N + BN - 1) / BN);
         const int grid = std::max(1, std::min(tiles, sms));
         a.group_n = choose_group_n((M + BM - 1) / BM, (N + BN - 1) / BN, grid, Kp, S);
