@@ -556,6 +556,12 @@ __global__ void __launch_bounds__(256) k_residual(const double* Z, const double*
     }
 }
 
+// Y <- Y - sigma Q (the shift of a power step)
+__global__ void k_shift(double* Y, const double* Q, double sigma, int64_t count) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x)
+        Y[i] = fma(-sigma, Q[i], Y[i]);
+}
+
 // U[r*dn + i] = QW[i*n + r]
 __global__ void k_to_isometry(const double* QW, int64_t n, int dn, double* U) {
     const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -723,7 +729,7 @@ int isometry(Ctx& ctx, const double* M, int64_t n, int dcut, double* U, std::vec
         m_slices = sp;
         m_e = ep;
     }
-    auto apply_m = [&]() {
+    auto apply_m = [&](double shift) {
         GemmDesc g;
         g.M = n; g.N = m; g.K = n;
         g.A = gm;
@@ -733,6 +739,23 @@ int isometry(Ctx& ctx, const double* M, int64_t n, int dcut, double* U, std::vec
         g.C = Y; g.c_m = ctx.table({{n, 1}}); g.c_n = ctx.table({{m, n}}); g.beta = 0.0;
         g.allow_ksplit = true;    // n / 128 tiles of 128 x m: K is split over the idle SMs
         gemm(ctx, g, precision);
+        if (shift > 0.0) {
+            const int64_t cnt = n * m;
+            k_shift<<<(unsigned)std::min<int64_t>((cnt + 255) / 256, 4 * ctx.sm_count), 256, 0, ctx.stream>>>(
+                Y, Q, shift, cnt);
+            TRG_LAUNCHED(ctx);
+        }
+    };
+    // Power steps apply M - sigma I with sigma = theta_m / 2 (a degree-one
+    // Chebyshev filter of the unwanted interval [0, theta_m]): the
+    // components outside the block shrink by (theta_m / 2) / (theta_dn -
+    // theta_m / 2) a step instead of theta_m / theta_dn, at the cost of one
+    // axpy.  theta_m comes from the last Rayleigh-Ritz step, or from the
+    // previous solve of this direction before the first; a Rayleigh-Ritz
+    // product is never shifted.
+    auto shifted_rate = [](double th_m, double th_dn) {
+        if (!(th_m > 0.0) || !(th_dn > th_m)) return 0.98;
+        return std::min(std::max(0.5 * th_m / (th_dn - 0.5 * th_m), 0.05), 0.98);
     };
     // The number of products that reached the tolerance in the previous solve
     // of this direction (same sizes) is the plan: the spectra of successive
@@ -741,13 +764,14 @@ int isometry(Ctx& ctx, const double* M, int64_t n, int dcut, double* U, std::vec
     // a first, FP32-only Rayleigh-Ritz that measures the convergence rate.
     Ctx::EigHint& hint = ctx.eig_hint[step & 1];
     const bool have_hint = hint.n == n && hint.m == m && hint.precision == precision && hint.products > 0;
+    double sigma = (have_hint && hint.theta_m > 0.0) ? 0.5 * hint.theta_m : 0.0;
     // the start block is followed by power steps unless the first step is a
     // Rayleigh-Ritz step (no plan and m = n)
     orthonormalise(ctx, Q, n, m, G, L, flags, nbad, seed, salt, have_hint || m < n);
     int applied = 0;                 // products of M in the span of Q
     if (!have_hint) {
         for (int pre = 0; pre < 2 && m < n; ++pre) {
-            apply_m();
+            apply_m(0.0);
             std::swap(Q, Y);
             orthonormalise(ctx, Q, n, m, G, L, flags, nbad, seed, salt, pre == 0);
             ++applied;
@@ -773,7 +797,7 @@ int isometry(Ctx& ctx, const double* M, int64_t n, int dcut, double* U, std::vec
     int since_rr = 0;                // products applied since the previous Rayleigh-Ritz
     for (int it = 1; it <= max_it; ++it) {
         if (pending > 0) {
-            apply_m();
+            apply_m(sigma);
             std::swap(Q, Y);
             orthonormalise(ctx, Q, n, m, G, L, flags, nbad, seed, salt, pending > 1);
             --pending;
@@ -783,7 +807,7 @@ int isometry(Ctx& ctx, const double* M, int64_t n, int dcut, double* U, std::vec
             continue;
         }
         // Y = M Q
-        apply_m();
+        apply_m(0.0);
         // Rayleigh-Ritz
         gram(ctx, Q, Y, n, m, G, TRG_FP64);
         TRG_CUDA(cudaMemsetAsync(sweeps, 0, 2 * sizeof(int), ctx.stream));
@@ -870,10 +894,13 @@ int isometry(Ctx& ctx, const double* M, int64_t n, int dcut, double* U, std::vec
                 // products beyond what the tolerance needed (at the rate
                 // theta_m / theta_dn), two kept spare: a plan that falls short
                 // costs a second Rayleigh-Ritz, several times a product.
-                const double r = std::min(std::max(th[(size_t)m - 1] / th[(size_t)dn_paper - 1], 0.05), 0.98);
+                const double r = sigma > 0.0
+                                     ? shifted_rate(th[(size_t)m - 1], th[(size_t)dn_paper - 1])
+                                     : std::min(std::max(th[(size_t)m - 1] / th[(size_t)dn_paper - 1], 0.05), 0.98);
                 const int slack = (res > 0.0 && res < tol) ? (int)std::floor(std::log(tol / res) / -std::log(r)) : 0;
                 hint.n = n; hint.m = m; hint.precision = precision;
                 hint.products = std::max(1, applied - std::max(0, slack - 2));
+                hint.theta_m = m < n ? th[(size_t)m - 1] : 0.0;
             }
             int dn = dn_paper;
             if (ctx.cfg.trunc == TRG_TRUNC_MULTIPLET && dn < n) {
@@ -890,8 +917,11 @@ int isometry(Ctx& ctx, const double* M, int64_t n, int dcut, double* U, std::vec
             TRG_LAUNCHED(ctx);
             return dn;
         }
-        // plan the power steps to the next Rayleigh-Ritz
-        double rho = th[(size_t)m - 1] / th[(size_t)dn_paper - 1];
+        // plan the power steps to the next Rayleigh-Ritz (shifted by the
+        // fresh theta_m)
+        sigma = (m < n && th[(size_t)m - 1] > 0.0) ? 0.5 * th[(size_t)m - 1] : 0.0;
+        double rho = sigma > 0.0 ? shifted_rate(th[(size_t)m - 1], th[(size_t)dn_paper - 1])
+                                 : th[(size_t)m - 1] / th[(size_t)dn_paper - 1];
         if (rr_done > 0 && prev_res > 0.0 && res > 0.0 && since_rr > 0)
             rho = std::max(rho, std::pow(res / prev_res, 1.0 / since_rr));
         rho = std::min(std::max(rho, 0.05), 0.98);

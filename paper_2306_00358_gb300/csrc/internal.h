@@ -132,7 +132,9 @@ struct Ctx {
     uint64_t counters[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     // Subspace iteration: power steps that reached the tolerance in the last
     // solve of each direction (x / y half-steps), used as the next plan.
-    struct EigHint { int64_t n = -1; int m = -1; int precision = -1; int products = 0; };
+    // plan of the next isometry of one direction: the products its
+    // predecessor needed and that solve's smallest Ritz value theta_m
+    struct EigHint { int64_t n = -1; int m = -1; int precision = -1; int products = 0; double theta_m = 0.0; };
     EigHint eig_hint[2];
     cudaEvent_t get_event();
     // Record the start of a timed region of phase p (no-op unless profiling).
