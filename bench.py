@@ -242,8 +242,8 @@ def load_peaks():
 # that file is unchanged, else null.  The autotuner picks among tile orders
 # by time, and orders of equal time differ in L2 reuse, so the bytes of a
 # run can differ from the capture's by the order it picked.
-SPLIT_MMA_TRAFFIC = {"sha256": "34c9ef3dc262296c8145ded25cbfa7b7f377cb406af82e2919ed1fe07fbc6679",
-                     "bytes_per_launch": 1.5232e10}
+SPLIT_MMA_TRAFFIC = {"sha256": "bb6c8ac231f7fc9b99737c0477f6b0d4aa10d3225d283afec574745938a0ba9a",
+                     "bytes_per_launch": 1.5233e10}
 # Algorithmic bytes of one X2 launch at Dcut 64, S = 4: read the A slices
 # (S x 65536 x 4096 BF16) and the B slices (S x 4096 x 4096 BF16), write the
 # next product's A slices (S x 65536 x 4096 BF16) and row exponents.

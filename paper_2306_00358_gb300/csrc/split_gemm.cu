@@ -1190,6 +1190,75 @@ __global__ void __launch_bounds__(256) k_slice_contig(const double* __restrict__
     }
 }
 
+// The S BF16 slices (bits) of x in a row with |x| < 2^ea: the fixed-point
+// value X = rint(x 2^(F - ea)) (halves away from zero), F = 7 + 8 (S - 1),
+// as S signed base-256 digits, each exact in BF16.  The arithmetic of
+// k_slice and k_slice_contig, element for element.
+template <int S>
+__device__ __forceinline__ void slice_bits(double x, int ea, uint16_t (&h)[S]) {
+    constexpr int F = 7 + 8 * (S - 1);
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const int ex = (int)((b >> 52) & 0x7FF);
+    long long X = 0;
+    if (ex) {
+        const int shift = 52 + 1023 + ea - ex - F;     // >= 53 - F > 0
+        if (shift < 63) {
+            const unsigned long long m53 = (b & ((1ull << 52) - 1)) | (1ull << 52);
+            X = (long long)((m53 + (1ull << (shift - 1))) >> shift);
+            if (b >> 63) X = -X;
+        }
+    }
+    int d[S];
+#pragma unroll
+    for (int p = S - 1; p >= 1; --p) {
+        const int lo = (int)(((X + 128) & 255) - 128);
+        d[p] = lo;
+        X = (X - lo) >> 8;
+    }
+    d[0] = (int)X;
+#pragma unroll
+    for (int p = 0; p < S; ++p) {
+        const float f = (__int_as_float(0x4B400000 + d[p]) - 12582912.0f) * __int_as_float((127 - 8 * p) << 23);
+        h[p] = (uint16_t)(__float_as_uint(f) >> 16);
+    }
+}
+
+// Exponents and slices of a few rows in one launch (the n x m blocks the
+// isometry multiplies by M: m rows of n as a B operand): a CTA per row r < Rp
+// takes the largest exponent field of its row (e_row[r] = field - 1022,
+// -1022 for a zero row, as row_exponents gives it), then writes the row's
+// slices, reading the row a second time through L1 / L2.  Bit-identical to
+// row_exponents followed by k_slice.
+template <int S>
+__global__ void __launch_bounds__(256) k_slice_rows(const double* __restrict__ src, const int64_t* __restrict__ off_r,
+                                                    const int64_t* __restrict__ off_c, int R, int K, int Rp, int Kp,
+                                                    int* __restrict__ e_row, uint16_t* __restrict__ out) {
+    __shared__ int wmax[8];
+    const int r = blockIdx.x;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const bool real = r < R;
+    const double* row = real ? src + off_r[r] : src;
+    unsigned ef = 0;
+    if (real)
+        for (int k = threadIdx.x; k < K; k += 256)
+            ef = max(ef, (unsigned)(((unsigned long long)__double_as_longlong(row[off_c[k]]) >> 52) & 0x7FF));
+    ef = __reduce_max_sync(0xffffffffu, ef);
+    if (lane == 0) wmax[warp] = (int)ef;
+    __syncthreads();
+    int mx = 0;
+#pragma unroll
+    for (int w = 0; w < 8; ++w) mx = max(mx, wmax[w]);
+    const int ea = mx ? mx - 1022 : -1022;
+    if (real && threadIdx.x == 0) e_row[r] = ea;
+    const size_t plane = (size_t)Rp * Kp;
+    for (int k = threadIdx.x; k < Kp; k += 256) {
+        uint16_t h[S];
+        slice_bits<S>((real && k < K) ? row[off_c[k]] : 0.0, ea, h);
+#pragma unroll
+        for (int p = 0; p < S; ++p) out[p * plane + (size_t)r * Kp + k] = h[p];
+    }
+}
+
 // ------------------------------------------------------------- host side ---
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
     static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
@@ -1335,6 +1404,22 @@ void launch_slice(Ctx& ctx, const Gather& g, int R, int K, int Rp, int Kp, const
     dim3 grid((unsigned)((Kp + SL_K - 1) / SL_K), (unsigned)std::min<int64_t>((Rp + SL_R - 1) / SL_R, 65535));
     k_slice<S><<<grid, 256, 0, ctx.stream>>>(g.base, g.off_r, g.off_c, R, K, Rp, Kp, g.c_fast ? 1 : 0, e, out);
     TRG_LAUNCHED(ctx);
+}
+
+void row_exponents(Ctx& ctx, const Gather& g, int R, int K, int* e);
+
+// Exponents and slices of an operand (rows r < R of length K, padded to Rp x
+// Kp): one launch for at most SLICE_ROWS_MAX rows, else the two passes.
+constexpr int SLICE_ROWS_MAX = 256;
+template <int S>
+void exponents_and_slices(Ctx& ctx, const Gather& g, int R, int K, int Rp, int Kp, int* e, uint16_t* out) {
+    if (Rp <= SLICE_ROWS_MAX) {
+        k_slice_rows<S><<<(unsigned)Rp, 256, 0, ctx.stream>>>(g.base, g.off_r, g.off_c, R, K, Rp, Kp, e, out);
+        TRG_LAUNCHED(ctx);
+        return;
+    }
+    row_exponents(ctx, g, R, K, e);
+    launch_slice<S>(ctx, g, R, K, Rp, Kp, e, out);
 }
 
 void row_exponents(Ctx& ctx, const Gather& g, int R, int K, int* e) {
@@ -1508,16 +1593,15 @@ void gemm_split(Ctx& ctx, const GemmDesc& d) {
     } else {
         row_exponents(ctx, d.A, M, K, ea);
     }
-    if (!pre_b) row_exponents(ctx, bt2, N, K, eb);
     switch (S) {
         case 2: if (!pre_a) launch_slice<2>(ctx, d.A, M, K, Mp, Kp, ea, sa);
-                if (!pre_b) launch_slice<2>(ctx, bt2, N, K, Np, Kp, eb, sb); break;
+                if (!pre_b) exponents_and_slices<2>(ctx, bt2, N, K, Np, Kp, eb, sb); break;
         case 3: if (!pre_a) launch_slice<3>(ctx, d.A, M, K, Mp, Kp, ea, sa);
-                if (!pre_b) launch_slice<3>(ctx, bt2, N, K, Np, Kp, eb, sb); break;
+                if (!pre_b) exponents_and_slices<3>(ctx, bt2, N, K, Np, Kp, eb, sb); break;
         case 4: if (!pre_a) launch_slice<4>(ctx, d.A, M, K, Mp, Kp, ea, sa);
-                if (!pre_b) launch_slice<4>(ctx, bt2, N, K, Np, Kp, eb, sb); break;
+                if (!pre_b) exponents_and_slices<4>(ctx, bt2, N, K, Np, Kp, eb, sb); break;
         case 5: if (!pre_a) launch_slice<5>(ctx, d.A, M, K, Mp, Kp, ea, sa);
-                if (!pre_b) launch_slice<5>(ctx, bt2, N, K, Np, Kp, eb, sb); break;
+                if (!pre_b) exponents_and_slices<5>(ctx, bt2, N, K, Np, Kp, eb, sb); break;
         default: fail(TRG_EINVAL, "split_slices must be 2..5");
     }
     const CUtensorMap ta = make_map(sa, S * Mp, Kp);
