@@ -201,6 +201,13 @@ def oracle_half_step_sample():
     return total, desc
 
 
+def workload_config(precision: str, world: int, shard: bool) -> dict:
+    """The workload this bench times (both arms print the same)."""
+    return {"workload": WORKLOAD, "precision": precision, "dcut": DCUT,
+            "l2": "inputs larger than L2 (T 134 MB, M 134 MB, workspace >= 1 GB per step)",
+            "parallelism": ("j-sharded solve" if shard else "replicas") if world > 1 else "single"}
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -220,9 +227,12 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "s/half-step", "n_gpus": args.gpus,
             "steps": steps, "warmup": args.warmup, "ms_per_step": val * 1e3, "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD + " (oracle sample, scaled)", "dcut": DCUT},
+            "config": workload_config(args.precision or "split", int(os.environ.get("WORLD_SIZE", "1")),
+                                      args.shard and int(os.environ.get("WORLD_SIZE", "1")) > 1),
             "cpu_baseline": {"value": val, "unit": "s/half-step", "cores": cores, "kind": "oracle", "sample": desc},
             "e2e": {"value": val, "unit": "s/half-step", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "value_kind": "the oracle timed on a bounded sample of each half-step and scaled to the whole "
+                          "(see cpu_baseline.sample); wall_s is the time the samples took",
             "wall_s": wall}
     print(json.dumps(line), flush=True)
 
@@ -530,9 +540,7 @@ def run_native(args):
                 "scaling": "strong" if shard else "weak",
                 "vs_baseline": None, "dtype": "f64" if precision == "fp64" else "bf16-slices(x%d)->f64" % args.slices,
                 "data": "synthetic",
-                "config": {"workload": WORKLOAD, "precision": precision, "dcut": DCUT,
-                           "l2": "inputs larger than L2 (T 134 MB, M 134 MB, workspace >= 1 GB per step)",
-                           "parallelism": ("j-sharded solve" if shard else "replicas") if world > 1 else "single"},
+                "config": workload_config(precision, world, shard),
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
                 "phases_ms": {k: round(v["ms"], 3) for k, v in ph.items()}, "counters": counters, "solve": solve,
                 "calibration": calib, "accuracy": acc, "serve_sample": serve}
