@@ -483,7 +483,8 @@ int trg_profile_read(trg_ctx* ctx, int phase, trg_phase_stats* out);
 
 /* Diagnostic counters since trg_create: out[0] subspace iterations,
  * out[1] Rayleigh-Ritz solves, out[2] FP32 Jacobi sweeps, out[3] FP64
- * Jacobi sweeps, out[4] Cholesky-QR column repairs, out[5] second
+ * Jacobi sweeps (sweeps that rotated; after the FP64 refinement of the
+ * eigenbasis usually none), out[4] Cholesky-QR column repairs, out[5] second
  * Cholesky-QR passes left out between power steps, out[6] product shapes
  * whose launch choice this context timed (autotune); n <= 8 entries. */
 int trg_get_counters(const trg_ctx* ctx, uint64_t* out, int n);
